@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the TLS period-grid search: Kepler-like light curves per hour.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gtls|reference]
+                    [--workload kepler_like|short_white|long_baseline]
+
+One step is one complete search of one light curve (fold, sort, every
+duration and T0 window, SR and SDE) on one GPU.  The default workload is the
+Kepler-like 1460-day curve (29.4-min cadence with quarter gaps and 10 %
+dropouts, ~64k points, period grid 0.5-730 d).  Under torchrun (N > 1) every
+rank searches its own replica (weak scaling); there is no collective on the
+data path.  Rank 0 prints one JSON line.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload and prints the same JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Kepler-like light curves/hour on 1 GB300 (plain vs batched+learned, equal recall)"
+UNIT = "light curves/hour"
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM (4 x 32)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gtls", choices=["gtls", "reference"])
+    ap.add_argument("--workload", default="kepler_like",
+                    choices=["kepler_like", "short_white", "long_baseline"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample (cpu_baseline / reference step)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    import synth
+    return synth.make_workload(name)
+
+
+def _describe(lc, info):
+    cfg = lc.search
+    return {
+        "workload": f"{lc.name}: {lc.baseline_days:.0f}-day baseline, n={lc.n} points, "
+                    f"{info['n_periods']} trial periods {cfg['period_min_days']}-"
+                    f"{cfg['period_max_days']:.0f} d (Ofir, OS=3), dt0=0.05",
+        "n_points": lc.n,
+        "n_periods": info["n_periods"],
+        "window_point_evaluations": info["wpe"],
+        "seed": lc.seed,
+        "l2": "flushed before every timed step (256 MiB write; L2 is 129 MB)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() in ("active", "0x1", "1", "yes"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2607_00348_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(workload):
+    """DRAM bytes per window-search launch from a committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", f"window_search_{workload}.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_sha") != _kernel_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def oracle_sample(lc, cpu_seconds):
+    """Time the FP64 oracle on a bounded, evenly spread subset of the periods.
+
+    Returns (light curves/hour extrapolated by window-point evaluations,
+    threads, sample description)."""
+    import numpy as np
+    from oracle import grid
+    from oracle import search as osr
+    cfg = lc.search
+    op = osr.plan(lc.n, lc.baseline_days, period_min_days=cfg["period_min_days"],
+                  period_max_days=cfg["period_max_days"])
+    npd = op.periods.size
+    d = op.dur_pts.astype(np.int64)
+    st = np.array([grid.t0_stride(int(v), op.dt0) for v in d], dtype=np.int64)
+    w_j = (-(-lc.n // st)) * d                       # ceil(n / st) windows of D points
+    j = np.arange(d.size)[None, :]
+    first = np.concatenate([[True], d[1:] != d[:-1]])[None, :]
+    lo, hi = op.jlo[:, None], op.jhi[:, None]
+    kept = (j >= lo) & (j <= hi) & ((j == lo) | first)
+    wpe_p = (kept * w_j[None, :]).sum(axis=1).astype(np.float64)
+    wpe_full = float(wpe_p.sum())
+    threads = osr.threads_used()
+    probe = np.linspace(0, npd - 1, min(npd, 2 * threads)).astype(np.int64)
+    t0 = time.perf_counter()
+    osr.search_periods(op, lc.t, lc.y, lc.dy, probe)
+    rate = float(wpe_p[probe].sum()) / max(time.perf_counter() - t0, 1e-6)
+    k = int(max(threads, min(npd, round(cpu_seconds * rate / (wpe_full / npd)))))
+    sel = np.unique(np.linspace(0, npd - 1, k).astype(np.int64))
+    t0 = time.perf_counter()
+    osr.search_periods(op, lc.t, lc.y, lc.dy, sel)
+    dt = time.perf_counter() - t0
+    frac = float(wpe_p[sel].sum()) / wpe_full
+    sec_full = dt / frac
+    desc = (f"{sel.size} of {npd} periods evenly spread ({100 * frac:.2f} % of the window-point "
+            f"evaluations), {dt:.1f} s on {threads} threads, extrapolated by WPE to "
+            f"{sec_full:.0f} s per light curve")
+    return 3600.0 / sec_full, threads, desc, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    lc = _workload(args.workload)
+    vals, secs = [], []
+    last = None
+    for i in range(args.warmup + args.steps):
+        v, threads, desc, dt = oracle_sample(lc, args.cpu_seconds)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+        last = (threads, desc)
+    value = statistics.median(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 3600.0 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded numpy generator)",
+        "config": {"workload": f"{lc.name}: n={lc.n} points, oracle on a period sample per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last[0], "kind": "oracle",
+                         "sample": last[1]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gtls(args):
+    import numpy as np
+    import torch
+
+    import paper_2607_00348_gb300 as pkg
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.load()
+
+    lc = _workload(args.workload)
+    cfg = lc.search
+    plan = pkg.Plan(pkg.PlanConfig(baseline_days=lc.baseline_days, n_points=lc.n,
+                                   period_min_days=cfg["period_min_days"],
+                                   period_max_days=cfg["period_max_days"]))
+    info = {"n_periods": plan.n_periods, "wpe": float(plan.info.wpe),
+            "n_windows": int(plan.info.n_windows)}
+    t = torch.as_tensor(lc.t, dtype=torch.float64, device=dev)
+    y = torch.as_tensor(lc.y, dtype=torch.float64, device=dev)
+    dy = torch.as_tensor(lc.dy, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        res = plan.search(t, y, dy, stream=stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    plan.set_profiling(True)
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    win_ms, stage = [], []
+    launches = 0
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)                 # evict the previous step from L2
+        starts[k].record(stream)
+        res = plan.search(t, y, dy, stream=stream)
+        ends[k].record(stream)
+        pr = plan.profile()
+        win_ms.append(pr.ms_window_search)
+        stage.append(pr.as_dict())
+        launches += int(pr.kernel_launches)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    plan.set_profiling(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1000.0
+    if ws > 1:
+        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(tt.item())
+    value = ws * args.steps * 3600.0 / total_s
+
+    # end to end: host arrays in pinned memory -> device -> result back
+    e2e = None
+    if not args.no_e2e:
+        th = torch.from_numpy(lc.t).pin_memory()
+        yh = torch.from_numpy(lc.y).pin_memory()
+        dh = torch.from_numpy(lc.dy).pin_memory()
+        plan.search_host(th.numpy(), yh.numpy(), dh.numpy(), stream=stream)
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            plan.search_host(th.numpy(), yh.numpy(), dh.numpy(), stream=stream)
+        w1 = time.perf_counter()
+        e_s = w1 - w0
+        if ws > 1:
+            tt = torch.tensor([e_s], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e_s = float(tt.item())
+        import ctypes
+        e2e = {"value": ws * args.steps * 3600.0 / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * lc.n,
+               "d2h_bytes_per_step": ctypes.sizeof(pkg.Result) + 4}
+
+    if rank != 0:
+        plan.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = 2.0 * props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    win_s = statistics.mean(win_ms) / 1000.0
+    achieved = 2.0 * info["wpe"] / win_s / 1e12        # 1 FMA per window-point evaluation
+    traffic = _ncu_traffic(args.workload)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "k_window_search",
+                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 FMA "
+                              f"lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                "achieved_basis": "2 flop x window-point evaluations / mean window-search "
+                                  "stage time (CUDA events on the search stream)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, threads, desc, _ = oracle_sample(lc, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    mean_stage = {k: statistics.mean(s[k] for s in stage) for k in
+                  ("ms_prepare", "ms_fold_sort", "ms_window_search", "ms_finalize", "ms_sr_sde")}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded numpy generator, Kepler-like)",
+        "config": dict(_describe(lc, info), parallelism=f"replicas x{ws}"),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+        "stage_ms": mean_stage,
+        "result": {"period": res.period, "sde": res.sde, "depth": res.depth,
+                   "duration_days": res.duration_days},
+    }
+    print(json.dumps(out), flush=True)
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gtls(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * gtls.h -- C ABI of the GB300 TLS period-grid search (libgtls.so).
+ *
+ * The library implements the data-parallel search of the GTLS paper
+ * (arxiv 2607.00348, Sect. 2): for every trial period of an Ofir-sampled
+ * grid (Sect. 2.2.1) it folds the light curve (Eq. phase), sorts it by
+ * phase, slides a limb-darkened transit template of every trial duration
+ * (Sect. 2.2.2) over the folded curve with T0 steps of max(1, floor(D dt0))
+ * points (Eq. N_skip), fits the depth (Eqs. k, depth), evaluates chi2 of
+ * the model (Eqs. edge, out, in) and reduces the per-period minimum chi2(P)
+ * to the signal residue SR(P), SDE_raw(P) and the median-detrended SDE(P)
+ * (Sect. 2.4).  All search arithmetic runs in CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point:
+ *   - Returns a gtls_status; nothing is thrown across the ABI.  On failure
+ *     gtls_last_error() returns a message for the calling thread.
+ *   - Pointers documented as "device" must be CUDA device (or managed)
+ *     memory on the plan's device; "host" pointers are ordinary memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that return results in host structs synchronise that stream.
+ *   - A plan is not thread-safe: one search at a time per plan.
+ *
+ * Readings of the paper fixed by this ABI (the paper is silent on them):
+ *   - SR(P) = chi2_min / chi2(P) in (0, 1] (Kovacs convention; the paper's
+ *     printed ratio is inverted), 0/0 := 1.
+ *   - durations come from one geometric grid of T14/P (ratio dur_ratio);
+ *     a period searches the grid points inside its k_min/k_max/q_cap
+ *     envelope; D = max(1, round(q n)) points.
+ *   - the template is a central small-planet transit with quadratic limb
+ *     darkening (u1, u2): s_k = 1 - u1(1-mu) - u2(1-mu)^2,
+ *     mu = sqrt(1 - (2x-1)^2), x = (k + 1/2)/D.
+ *   - depth = max(0, mean in-window flux deficit / mean template value).
+ *   - phases are exact on a lattice of 2^-e days (e reported by
+ *     gtls_plan_get_info); ties in phase keep the input order.
+ *   - SDE(P) = SDE_raw(P) minus the running median of SDE_raw over an odd
+ *     window (median_window; default 2 floor(N_P/200) + 1), truncated at
+ *     the ends, lower median for even counts.
+ */
+#ifndef GTLS_H
+#define GTLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GTLS_OK = 0,
+    GTLS_ERR_INVALID_ARG = 1, /* bad sizes/parameters, non-finite input, dy <= 0 */
+    GTLS_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    GTLS_ERR_OOM = 3,         /* device or host allocation failed */
+    GTLS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+    GTLS_ERR_INTERNAL = 5     /* an internal consistency check failed */
+} gtls_status;
+
+typedef struct gtls_plan gtls_plan;
+
+/* Search configuration.  Fill with gtls_plan_params_default, then edit. */
+typedef struct {
+    double baseline_days;       /* S = t_max - t_min (days), > 0; sets A of Eq. (C, A) */
+    int64_t n_points;           /* points per light curve, >= 2; D = round(q n) */
+    double m_star, r_star;      /* stellar mass / radius in solar units (default 1, 1) */
+    double oversampling;        /* OS of Eq. (C, A) (default 3) */
+    double period_min_days;     /* 0 => Roche limit, Eq. (f_max) */
+    double period_max_days;     /* 0 => S / 2, Eq. (f_min) */
+    double k_min, k_max;        /* duration envelope, s^(2/3) (default 20.05, 620.84) */
+    double q_cap;               /* maximum T14/P (default 0.15) */
+    double dur_ratio;           /* geometric step of the T14/P grid (default 1.1) */
+    double dt0;                 /* T0 step as a fraction of D (default 0.05) */
+    double u1, u2;              /* quadratic limb darkening (default 0.4, 0.25) */
+    int32_t median_window;      /* odd SDE median window; 0 => 2 floor(N_P/200) + 1 */
+    int32_t reserved0;
+    const double* periods_days; /* optional explicit period grid (host, copied); NULL => Ofir */
+    int64_t n_periods;          /* length of periods_days */
+} gtls_plan_params;
+
+/* Sizes of a plan (host struct filled by gtls_plan_get_info). */
+typedef struct {
+    int64_t n_periods;          /* trial periods, ascending */
+    int64_t n_points;
+    int32_t n_durations;        /* points of the global T14/P grid */
+    int32_t time_exponent;      /* e: phases are exact on a 2^-e-day lattice */
+    int64_t max_duration_points;/* largest D of any period */
+    int64_t n_windows;          /* (period, duration, T0) triples per search */
+    double wpe;                 /* window-point evaluations per search: sum of D over windows */
+    int64_t device_bytes;       /* device memory the plan holds */
+    int32_t median_window;
+    int32_t periods_per_chunk;  /* periods folded and searched per kernel wave */
+} gtls_plan_info;
+
+/* Best candidate of one search (host struct). */
+typedef struct {
+    double period;        /* days, argmax of SDE(P) */
+    double duration_days; /* q_j * period */
+    double t0;            /* mid-transit time of the best window (days, input time system) */
+    double depth;         /* fitted depth (fraction) */
+    double sde;           /* SDE(P) at the best period */
+    double chi2;          /* chi2(P) at the best period */
+    double chi2_min;      /* global minimum of chi2(P) */
+    double chi2_0;        /* chi2 of the constant model, sum(((y-1)/dy)^2) */
+    int64_t period_idx;   /* index into the plan's period grid */
+    int32_t dur_idx;      /* index into the global T14/P grid */
+    int32_t dur_points;   /* D */
+    int64_t t0_idx;       /* window start in folded order (multiple of the T0 step) */
+    int32_t uniform_dy;   /* 1 if all dy were equal (uniform-weight kernel) */
+    int32_t reserved0;
+} gtls_result;
+
+/* Optional per-period outputs (device pointers, each nullable, n_periods long). */
+typedef struct {
+    double* chi2;     /* chi2(P) */
+    int32_t* dur_idx; /* argmin duration (global grid index) */
+    int32_t* t0_idx;  /* argmin window start in folded order */
+    double* depth;    /* depth at the argmin */
+    double* t0;       /* mid-transit time at the argmin (days) */
+    double* sr;       /* SR(P) */
+    double* sde_raw;  /* SDE_raw(P) */
+    double* sde;      /* SDE(P) */
+} gtls_period_outputs;
+
+/* Per-stage device time of the last search (host struct). */
+typedef struct {
+    double ms_prepare;        /* per-curve arrays, t_ref, chi2_0, input checks */
+    double ms_fold_sort;      /* fold + sort + gather + prefix sums, all chunks */
+    double ms_window_search;  /* depth fit + chi2 of every window, all chunks */
+    double ms_finalize;       /* per-period chi2(P), depth, T0 */
+    double ms_sr_sde;         /* SR, SDE_raw, running median, argmax */
+    int64_t kernel_launches;  /* kernels the last search launched */
+    int64_t window_search_launches;
+    int32_t enabled;          /* 1 if the times above were measured */
+    int32_t reserved0;
+} gtls_profile;
+
+/* Fill p with the defaults above (baseline_days and n_points set to 0). */
+void gtls_plan_params_default(gtls_plan_params* p);
+
+/*
+ * Build the period grid (Eqs. f_min, f_max, f_i, C/A, N), the T14/P grid
+ * and per-period ranges (Eqs. upper, lower), the template table and the
+ * phase lattice on the host in FP64; upload them and allocate the scratch
+ * the search needs on the current CUDA device.  The plan owns all of it.
+ * Errors: INVALID_ARG (n_points < 2, baseline <= 0, P_min >= P_max, a period
+ * with an empty duration range, a grid too large for the lattice), OOM, CUDA.
+ */
+gtls_status gtls_plan_create(const gtls_plan_params* p, gtls_plan** out);
+
+gtls_status gtls_plan_get_info(const gtls_plan* plan, gtls_plan_info* out);
+
+/* Copy the period grid (days, ascending; host array of n_periods). */
+gtls_status gtls_plan_get_periods(const gtls_plan* plan, double* periods_days);
+
+/* Copy the T14/P grid q_j and D_j (host arrays of n_durations). */
+gtls_status gtls_plan_get_durations(const gtls_plan* plan, double* q, int32_t* points);
+
+/* Copy each period's first / last T14/P grid index (host arrays of n_periods). */
+gtls_status gtls_plan_get_ranges(const gtls_plan* plan, int32_t* jlo, int32_t* jhi);
+
+/*
+ * Search one light curve.  t, y, dy: device arrays of n doubles (n must
+ * equal the plan's n_points); the caller owns them; they are read-only and
+ * must stay valid until the stream work completes.  y is flux normalised to
+ * 1, dy > 0.  Writes *out (host) after synchronising `stream`.  per_period
+ * (nullable) receives per-period device outputs.
+ * Errors: INVALID_ARG (n mismatch, NaN/inf in t/y/dy, dy <= 0), CUDA.
+ */
+gtls_status gtls_search(gtls_plan* plan, const double* t, const double* y,
+                        const double* dy, int64_t n, void* stream,
+                        gtls_result* out, const gtls_period_outputs* per_period);
+
+/*
+ * Same as gtls_search for host arrays: copies t, y, dy into plan-owned
+ * device buffers on `stream` first (the end-to-end call).
+ */
+gtls_status gtls_search_host(gtls_plan* plan, const double* t, const double* y,
+                             const double* dy, int64_t n, void* stream,
+                             gtls_result* out);
+
+/*
+ * Search n_lc light curves packed back to back (CSR): curve i is
+ * t[offsets[i] .. offsets[i+1]) and likewise y, dy (device arrays);
+ * offsets is a host array of n_lc + 1 entries; plans[i] must have been made
+ * for curve i's n (plans may repeat).  out: host array of n_lc results.
+ * Each result equals gtls_search on that curve alone.
+ */
+gtls_status gtls_search_batch(gtls_plan* const* plans, int64_t n_lc,
+                              const double* t, const double* y, const double* dy,
+                              const int64_t* offsets, void* stream,
+                              gtls_result* out);
+
+/*
+ * Measure per-stage device time with CUDA events on the search stream
+ * (on != 0) or stop measuring (on == 0; the default).  Measuring adds one
+ * event record per stage and chunk; it changes no result.
+ */
+gtls_status gtls_plan_set_profiling(gtls_plan* plan, int32_t on);
+
+/* Stage times and launch counts of the plan's last search (host struct). */
+gtls_status gtls_plan_get_profile(const gtls_plan* plan, gtls_profile* out);
+
+/* Release the plan's device and host memory (NULL is a no-op). */
+void gtls_plan_destroy(gtls_plan* plan);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* gtls_last_error(void);
+
+/* Name of a status code. */
+const char* gtls_status_string(gtls_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GTLS_H */

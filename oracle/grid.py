@@ -1,6 +1,8 @@
 """Search grids of the oracle: periods, durations, template, phase lattice.
 
 Plain numpy, FP64, one formula per line.  Test infrastructure only.
+Transcendental functions go through Python's ``math`` module (the C
+library's pow and cbrt), elementary arithmetic through numpy.
 
 Readings of the paper taken here (the paper is silent or garbled on these):
 
@@ -54,9 +56,9 @@ def ofir_frequencies(baseline_days, m_star=1.0, r_star=1.0, oversampling=3.0,
     f_min = 2.0 / s if not period_max_days else 1.0 / (period_max_days * DAY)
     f_max = roche_f_max(m_star, r_star) if not period_min_days else \
         1.0 / (period_min_days * DAY)
-    a = math.pow(2.0 * math.pi, 2.0 / 3.0) / math.pi * r / np.cbrt(gm) / (s * oversampling)
-    c = np.cbrt(f_min) - a / 3.0
-    n_real = (np.cbrt(f_max) - np.cbrt(f_min) + a / 3.0) * 3.0 / a
+    a = math.pow(2.0 * math.pi, 2.0 / 3.0) / math.pi * r / math.cbrt(gm) / (s * oversampling)
+    c = math.cbrt(f_min) - a / 3.0
+    n_real = (math.cbrt(f_max) - math.cbrt(f_min) + a / 3.0) * 3.0 / a
     n_int = int(math.ceil(n_real))
     i = np.arange(1, n_int + 1, dtype=np.float64)
     x = a / 3.0 * i + c
@@ -80,9 +82,11 @@ def duration_grid(periods_days, n_points, k_min=20.05, k_max=620.84,
     period, the first and last admissible j (Eqs. upper/lower, cap).
     """
     p_s = np.asarray(periods_days, dtype=np.float64) * DAY
-    lo = k_min * np.power(p_s, -2.0 / 3.0)
-    hi = np.minimum(q_cap, k_max * np.power(p_s, -2.0 / 3.0))
-    q_lo = k_min * math.pow(float(p_s.max()), -2.0 / 3.0)
+    # scalar libm pow per period (numpy's vectorised pow rounds differently)
+    p23 = np.array([math.pow(float(v), -2.0 / 3.0) for v in p_s])
+    lo = k_min * p23
+    hi = np.minimum(q_cap, k_max * p23)
+    q_lo = float(lo[int(np.argmax(p_s))])      # k_min P_max^(-2/3)
     q_top = float(hi.max())
     q = []
     j = 0

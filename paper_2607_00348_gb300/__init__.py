@@ -1,0 +1,16 @@
+"""GB300 TLS period-grid search (libgtls) and its ctypes binding.
+
+The search itself lives in ``csrc/`` (CUDA for sm_103a behind the C ABI of
+``include/gtls.h``); :mod:`.gtls` marshals arguments to it.
+"""
+
+from .gtls import (  # noqa: F401
+    GtlsError,
+    Plan,
+    PlanConfig,
+    Result,
+    load,
+    library_path,
+    search_batch,
+)
+from .build import build  # noqa: F401

@@ -1,0 +1,104 @@
+// Internal structures of libgtls shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gtls.h"
+#include "plan_host.h"
+
+namespace gtls {
+
+// Read-only plan tables on the device (passed to kernels by value).
+struct DevPlan {
+    int64_t n;
+    int32_t np;           // periods
+    int32_t nd;           // T14/P grid points
+    int32_t time_exponent;
+    int32_t idx_bits;
+    int32_t bucket_log2;
+    int32_t max_kept;
+    const double* periods;
+    const int64_t* p_lat;
+    const float* inv_p;
+    const int32_t* bucket_shift;
+    const uint32_t* bucket_mul;
+    const int32_t* jlo;
+    const int32_t* jhi;
+    const int32_t* dmax_p;
+    const int32_t* dpts;
+    const int32_t* stride;
+    const int64_t* tmpl_off;
+    const float* tmpl;
+    const float* inv_sum_t;   // 1 / sum_k s_k
+    const float* sum_t2;      // sum_k s_k^2
+    const double* sum_t;      // FP64 sum_k s_k
+    const double* q;
+};
+
+// Per-light-curve derived arrays (n long unless noted).
+struct DevCurve {
+    int64_t* d_lat;           // rint((t - t_ref) 2^e)
+    float* d_f;               // float(t - t_ref) (days): coarse cycle estimate
+    float* r32;               // float(1 - y)
+    long long* rfx;           // rint((1 - y) 2^40): exact window sums of r
+    float* w32;               // float(1 / dy^2)
+    double* scal;             // [0] t_ref [1] chi2_0 [2] uniform weight w (0 if not uniform)
+    unsigned long long* tmin_key;  // ordered key of min(t)
+    unsigned int* flags;      // bit0 non-finite, bit1 dy <= 0, bit2 dy not uniform
+    double* part;             // block partials of chi2_0
+};
+
+// Per-chunk scratch: `chunk` periods in flight.
+struct DevChunk {
+    int32_t chunk;
+    int64_t fold_stride;      // >= n
+    int64_t pad_stride;       // >= n + dmax + margin (folded, padded arrays)
+    unsigned long long* keys; // bucket-ordered fold keys
+    uint32_t* slot;           // arrival slot in the bucket
+    int32_t* sidx;            // folded order -> original index
+    float* rs;                // folded r, padded by the period's first D_m points
+    float* ws;                // folded w (per-point weights only)
+    float* wrs;               // folded w r (per-point weights only)
+    long long* pf;            // prefix sums of rfx over the padded folded curve
+};
+
+// Per-period outputs (np long) and the reduction scratch.
+struct DevPeriod {
+    unsigned long long* best; // packed (delta-chi2 key, j, window) minimum
+    double* chi2;
+    int32_t* dur;
+    int32_t* t0i;
+    double* depth;
+    double* t0;
+    double* sr;
+    double* sde_raw;
+    double* sde;
+    double* stats;            // [0] chi2_min [1] mean SR [2] std SR
+    gtls_result* result;      // device copy of the best candidate
+};
+
+}  // namespace gtls
+
+struct gtls_plan {
+    gtls::PlanHost host;
+    int device = -1;
+    gtls::DevPlan dp{};
+    gtls::DevCurve dc{};
+    gtls::DevChunk dk{};
+    gtls::DevPeriod dq{};
+    double* in_t = nullptr;   // plan-owned input buffers of gtls_search_host
+    double* in_y = nullptr;
+    double* in_dy = nullptr;
+    int64_t device_bytes = 0;
+    // stage profiling: events recorded on the search stream when enabled
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> event_stage;   // stage of the interval ending at event i
+    gtls_profile profile{};
+    void* allocs[64] = {};
+    int n_allocs = 0;
+};

@@ -1,0 +1,1019 @@
+// libgtls: the TLS period-grid search on one GPU (sm_103a).
+//
+// Pipeline of one search (all on `stream`):
+//   k_curve_minmax, k_curve_prep, k_curve_reduce   per-point derived arrays, chi2_0
+//   for every chunk of periods:
+//     k_fold_sort      fold on the exact phase lattice (Eq. phase), bucket
+//                      sort by (phase, index), gather the folded curve, pad it
+//                      with its first D_m points (Sect. 2.3.2) and build the
+//                      exact prefix sums that give every moving average
+//                      (Eq. cumsum)
+//     k_window_search  every duration and T0 start: depth (Eqs. k, depth),
+//                      chi2 - chi2_0 (Eqs. out, in), per-period minimum
+//     k_period_finalize chi2(P), depth, T0 of each period's minimum
+//   k_sr_stats, k_median_sde, k_best     SR, SDE_raw, SDE, argmax (Sect. 2.4)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gtls_internal.h"
+
+using namespace gtls;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gtls_status fail(gtls_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define GTLS_CUDA(call)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? GTLS_ERR_OOM : GTLS_ERR_CUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+constexpr int kFoldThreads = 1024;
+constexpr int kSearchThreads = 256;
+constexpr int kMedianThreads = 1024;
+constexpr int kMedianCap = 8192;       // values a median block sorts in shared memory
+constexpr double kRScale = 1099511627776.0;   // 2^40: fixed point of r = 1 - y
+constexpr int64_t kPadMargin = 64;
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long double_order_key(double v)
+{
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double double_from_order_key(unsigned long long k)
+{
+    unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+__device__ __forceinline__ unsigned int float_order_key(float v)
+{
+    unsigned int u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float float_from_order_key(unsigned int k)
+{
+    unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+
+// Exact lattice phase rho = d mod P (0 <= d < 2^62, P > 0).  The float
+// product gives the cycle count to within one; two integer corrections make
+// it exact.
+__device__ __forceinline__ long long lattice_rho(long long d, float d_f, long long p, float inv_p)
+{
+    long long c = (long long)floorf(d_f * inv_p);
+    long long r = d - c * p;
+    if (r < 0) r += p;
+    else if (r >= p) r -= p;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t fold_bucket(long long rho, int sh, uint32_t mul)
+{
+    return (uint32_t)((((unsigned long long)rho >> sh) * (unsigned long long)mul) >> 32);
+}
+
+// Exclusive scan of one long long per thread over a 1024-thread block.
+__device__ long long block_exclusive_scan(long long v, long long* warp_sums, long long* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        long long s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+        if (lane == nw - 1) *total = s;
+    }
+    __syncthreads();
+    const long long base = warp > 0 ? warp_sums[warp - 1] : 0;
+    const long long out = base + x - v;
+    __syncthreads();
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// per-curve preparation
+// ---------------------------------------------------------------------------
+
+__global__ void k_curve_minmax(const double* __restrict__ t, const double* __restrict__ y,
+                               const double* __restrict__ dy, int64_t n, DevCurve dc)
+{
+    unsigned long long kmin = ~0ull;
+    unsigned int fl = 0;
+    const double dy0 = dy[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double ti = t[i], yi = y[i], di = dy[i];
+        if (!isfinite(ti) || !isfinite(yi) || !isfinite(di)) fl |= 1u;
+        if (!(di > 0.0)) fl |= 2u;
+        if (di != dy0) fl |= 4u;
+        const unsigned long long k = double_order_key(ti);
+        kmin = k < kmin ? k : kmin;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kmin, o);
+        kmin = k2 < kmin ? k2 : kmin;
+        fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(dc.tmin_key, kmin);
+        if (fl) atomicOr(dc.flags, fl);
+    }
+}
+
+__global__ void k_curve_prep(const double* __restrict__ t, const double* __restrict__ y,
+                             const double* __restrict__ dy, int64_t n, int e, DevCurve dc)
+{
+    __shared__ double red[32];
+    const double t_ref = double_from_order_key(*dc.tmin_key);
+    const double scale = ldexp(1.0, e);
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double dt = t[i] - t_ref;
+        const double r = 1.0 - y[i];
+        const double w = 1.0 / (dy[i] * dy[i]);
+        dc.d_lat[i] = __double2ll_rn(dt * scale);
+        dc.d_f[i] = (float)dt;
+        dc.r32[i] = (float)r;
+        dc.rfx[i] = __double2ll_rn(r * kRScale);
+        dc.w32[i] = (float)w;
+        acc += w * r * r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        dc.part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_curve_reduce(int nparts, const double* __restrict__ dy, DevCurve dc)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += dc.part[i];
+    dc.scal[0] = double_from_order_key(*dc.tmin_key);
+    dc.scal[1] = s;
+    dc.scal[2] = (*dc.flags & 4u) ? 0.0 : 1.0 / (dy[0] * dy[0]);
+}
+
+// ---------------------------------------------------------------------------
+// fold + sort + gather + prefix sums (one block per period)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kFoldThreads)
+k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
+{
+    extern __shared__ unsigned char smem[];
+    const int nb = 1 << dp.bucket_log2;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* start = hist + nb;
+    long long* warp_sums = reinterpret_cast<long long*>(start + nb);
+    long long* total = warp_sums + 32;
+
+    const int slot_id = blockIdx.x;
+    const int p = p0 + slot_id;
+    if (p >= dp.np) return;
+    const int64_t n = dp.n;
+    const long long P = dp.p_lat[p];
+    const float inv_p = dp.inv_p[p];
+    const int sh = dp.bucket_shift[p];
+    const uint32_t mul = dp.bucket_mul[p];
+    const int ib = dp.idx_bits;
+    const unsigned long long idx_mask = (1ull << ib) - 1ull;
+    unsigned long long* keys = dk.keys + (int64_t)slot_id * dk.fold_stride;
+    uint32_t* slotv = dk.slot + (int64_t)slot_id * dk.fold_stride;
+    int32_t* sidx = dk.sidx + (int64_t)slot_id * dk.fold_stride;
+    float* rs = dk.rs + (int64_t)slot_id * dk.pad_stride;
+    float* ws = dk.ws ? dk.ws + (int64_t)slot_id * dk.pad_stride : nullptr;
+    float* wrs = dk.wrs ? dk.wrs + (int64_t)slot_id * dk.pad_stride : nullptr;
+    long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
+    const bool uniform = dc.scal[2] > 0.0;
+
+    if (threadIdx.x == 0) dq.best[p] = ~0ull;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+
+    // 1. lattice phase -> bucket, arrival slot inside the bucket
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const long long rho = lattice_rho(dc.d_lat[i], dc.d_f[i], P, inv_p);
+        const uint32_t b = fold_bucket(rho, sh, mul);
+        slotv[i] = atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+
+    // 2. bucket starts (exclusive scan of the histogram)
+    {
+        const int per = (nb + blockDim.x - 1) / blockDim.x;
+        const int b0 = threadIdx.x * per;
+        long long local = 0;
+        for (int b = b0; b < b0 + per && b < nb; ++b) local += hist[b];
+        long long run = block_exclusive_scan(local, warp_sums, total);
+        for (int b = b0; b < b0 + per && b < nb; ++b) {
+            start[b] = (uint32_t)run;
+            run += hist[b];
+        }
+    }
+    __syncthreads();
+
+    // 3. scatter keys (phase << idx_bits | index) into bucket order
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const long long rho = lattice_rho(dc.d_lat[i], dc.d_f[i], P, inv_p);
+        const uint32_t b = fold_bucket(rho, sh, mul);
+        keys[start[b] + slotv[i]] = ((unsigned long long)rho << ib) | (unsigned long long)i;
+    }
+    __syncthreads();
+
+    // 4. rank inside the bucket -> folded position; gather the folded curve
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+        const unsigned long long key = keys[q];
+        const long long rho = (long long)(key >> ib);
+        const uint32_t b = fold_bucket(rho, sh, mul);
+        const uint32_t lo = start[b], cnt = hist[b];
+        uint32_t rank = 0;
+        for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
+        const uint32_t pos = lo + rank;
+        const int32_t idx = (int32_t)(key & idx_mask);
+        sidx[pos] = idx;
+        rs[pos] = dc.r32[idx];
+        pf[pos + 1] = dc.rfx[idx];
+        if (!uniform) {
+            ws[pos] = dc.w32[idx];
+            wrs[pos] = dc.w32[idx] * dc.r32[idx];
+        }
+    }
+    __syncthreads();
+
+    // 5. inclusive prefix of rfx in folded order: pf[k+1] = sum_{u<=k} rfx
+    {
+        const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+        const int64_t k0 = threadIdx.x * per;
+        const int64_t k1 = min(n, k0 + per);
+        long long local = 0;
+        for (int64_t k = k0; k < k1; ++k) local += pf[k + 1];
+        long long run = block_exclusive_scan(local, warp_sums, total);
+        for (int64_t k = k0; k < k1; ++k) {
+            run += pf[k + 1];
+            pf[k + 1] = run;
+        }
+        if (threadIdx.x == 0) pf[0] = 0;
+    }
+    __syncthreads();
+
+    // 6. padding: the first D_m folded points repeat after position N-1
+    const int64_t dm = dp.dmax_p[p];
+    const long long tot = pf[n];
+    for (int64_t k = threadIdx.x; k < dm + kPadMargin; k += blockDim.x) {
+        const bool real = k < dm;
+        rs[n + k] = real ? rs[k] : 0.0f;
+        if (!uniform) {
+            ws[n + k] = real ? ws[k] : 0.0f;
+            wrs[n + k] = real ? wrs[k] : 0.0f;
+        }
+        if (real) pf[n + k + 1] = tot + pf[k + 1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// window search: one thread per (period, duration, T0 start)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int kept_j(const DevPlan& dp, int p, int slot)
+{
+    const int lo = dp.jlo[p], hi = dp.jhi[p];
+    int c = -1;
+    for (int j = lo; j <= hi; ++j) {
+        if (j > lo && dp.dpts[j] == dp.dpts[j - 1]) continue;
+        if (++c == slot) return j;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(kSearchThreads)
+k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
+{
+    __shared__ unsigned long long red[kSearchThreads / 32];
+    const int slot_id = blockIdx.z;
+    const int p = p0 + slot_id;
+    if (p >= dp.np) return;
+    const int j = kept_j(dp, p, blockIdx.y);
+    if (j < 0) return;
+    const int d = dp.dpts[j], st = dp.stride[j];
+    const int64_t n = dp.n;
+    const int64_t nwin = (n + st - 1) / st;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if ((int64_t)blockIdx.x * blockDim.x >= nwin) return;  // whole block past the end
+    unsigned long long packed = ~0ull;
+    if (m < nwin) {
+        const int64_t s = m * st;
+        const float* rs = dk.rs + (int64_t)slot_id * dk.pad_stride + s;
+        const long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
+        const float* tm = dp.tmpl + dp.tmpl_off[j];
+        const double w_uni = dc.scal[2];
+        const long long sfx = pf[s + d] - pf[s];
+        const float sum_r = (float)((double)sfx * (1.0 / kRScale));
+        const float depth = fmaxf(0.0f, sum_r * dp.inv_sum_t[j]);
+        float dchi;
+        if (w_uni > 0.0) {
+            float c1 = 0.0f;
+            for (int k = 0; k < d; ++k) c1 = fmaf(rs[k], tm[k], c1);
+            dchi = (float)w_uni * depth * fmaf(depth, dp.sum_t2[j], -2.0f * c1);
+        } else {
+            const float* wr = dk.wrs + (int64_t)slot_id * dk.pad_stride + s;
+            const float* ww = dk.ws + (int64_t)slot_id * dk.pad_stride + s;
+            float c1 = 0.0f, c2 = 0.0f;
+            for (int k = 0; k < d; ++k) {
+                c1 = fmaf(wr[k], tm[k], c1);
+                c2 = fmaf(ww[k] * tm[k], tm[k], c2);
+            }
+            dchi = depth * fmaf(depth, c2, -2.0f * c1);
+        }
+        packed = ((unsigned long long)float_order_key(dchi) << 32) |
+                 ((unsigned long long)j << 24) | (unsigned long long)m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, packed, o);
+        packed = v < packed ? v : packed;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = packed;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = red[0];
+        for (int w = 1; w < kSearchThreads / 32; ++w) b = red[w] < b ? red[w] : b;
+        atomicMin(&dq.best[p], b);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-period result: chi2(P), depth, T0 of the minimum
+// ---------------------------------------------------------------------------
+
+__global__ void k_period_finalize(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, int cnt)
+{
+    const int slot_id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot_id >= cnt) return;
+    const int p = p0 + slot_id;
+    if (p >= dp.np) return;
+    const unsigned long long b = dq.best[p];
+    const float dchi = float_from_order_key((unsigned int)(b >> 32));
+    const int j = (int)((b >> 24) & 0xffull);
+    const int64_t m = (int64_t)(b & 0xffffffull);
+    const int d = dp.dpts[j], st = dp.stride[j];
+    const int64_t s = m * st;
+    const int64_t n = dp.n;
+    const long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
+    const double sum_r = (double)(pf[s + d] - pf[s]) * (1.0 / kRScale);
+    const double depth = fmax(0.0, sum_r / dp.sum_t[j]);
+    const int64_t c = (s + d / 2) % n;
+    const int32_t idx = dk.sidx[(int64_t)slot_id * dk.fold_stride + c];
+    const long long rho = lattice_rho(dc.d_lat[idx], dc.d_f[idx], dp.p_lat[p], dp.inv_p[p]);
+    dq.chi2[p] = dc.scal[1] + (double)dchi;
+    dq.dur[p] = j;
+    dq.t0i[p] = (int32_t)s;
+    dq.depth[p] = depth;
+    dq.t0[p] = dc.scal[0] + ldexp((double)rho, -dp.time_exponent);
+}
+
+// ---------------------------------------------------------------------------
+// SR, SDE_raw (one block), median detrending, argmax
+// ---------------------------------------------------------------------------
+
+__device__ double block_sum_fixed(double v, double* sh)
+{
+    // fixed-order tree over the block: deterministic for a given block size
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_sr_stats(int np, DevPeriod dq)
+{
+    __shared__ double sh[1024];
+    double mn = INFINITY;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) mn = fmin(mn, dq.chi2[i]);
+    sh[threadIdx.x] = mn;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const double cmin = sh[0];
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const double c = dq.chi2[i];
+        const double sr = c > 0.0 ? cmin / c : 1.0;
+        dq.sr[i] = sr;
+        acc += sr;
+    }
+    const double mean = block_sum_fixed(acc, sh) / (double)np;
+    acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const double dd = dq.sr[i] - mean;
+        acc += dd * dd;
+    }
+    const double var = block_sum_fixed(acc, sh) / (double)np;
+    const double sd = sqrt(var);
+    for (int i = threadIdx.x; i < np; i += blockDim.x)
+        dq.sde_raw[i] = sd > 1e-12 ? (dq.sr[i] - mean) / sd : 0.0;
+    if (threadIdx.x == 0) {
+        dq.stats[0] = cmin;
+        dq.stats[1] = mean;
+        dq.stats[2] = sd;
+    }
+}
+
+// Lower running median of sde_raw over [i-h, i+h] (truncated), one block per
+// `outs` consecutive outputs: the block sorts the union of its windows once
+// (bitonic, by value then position) and every thread walks the sorted list.
+__global__ void __launch_bounds__(kMedianThreads) k_median_sde(int np, int h, int outs, DevPeriod dq)
+{
+    extern __shared__ unsigned char smem[];
+    double* val = reinterpret_cast<double*>(smem);
+    int* pos = reinterpret_cast<int*>(val + kMedianCap);
+    const int i0 = blockIdx.x * outs;
+    const int lo = max(0, i0 - h);
+    const int hi = min(np - 1, i0 + outs - 1 + h);
+    const int len = hi - lo + 1;
+    int cap = 1;
+    while (cap < len) cap <<= 1;
+    for (int k = threadIdx.x; k < cap; k += blockDim.x) {
+        if (k < len) {
+            val[k] = dq.sde_raw[lo + k];
+            pos[k] = lo + k;
+        } else {
+            val[k] = INFINITY;
+            pos[k] = 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    for (int size = 2; size <= cap; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = threadIdx.x; k < cap; k += blockDim.x) {
+                const int l = k ^ stride;
+                if (l > k) {
+                    const bool up = (k & size) == 0;
+                    const bool gt = val[k] > val[l] || (val[k] == val[l] && pos[k] > pos[l]);
+                    if (gt == up) {
+                        const double tv = val[k];
+                        val[k] = val[l];
+                        val[l] = tv;
+                        const int tp = pos[k];
+                        pos[k] = pos[l];
+                        pos[l] = tp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < outs; t += blockDim.x) {
+        const int i = i0 + t;
+        if (i >= np) break;
+        const int wlo = max(0, i - h), whi = min(np - 1, i + h);
+        const int want = (whi - wlo) / 2;  // lower median: index (cnt-1)/2
+        int seen = 0;
+        double med = 0.0;
+        for (int k = 0; k < len; ++k) {
+            const int q = pos[k];
+            if (q >= wlo && q <= whi) {
+                if (seen == want) {
+                    med = val[k];
+                    break;
+                }
+                ++seen;
+            }
+        }
+        dq.sde[i] = dq.sde_raw[i] - med;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPeriod dq)
+{
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    double v = -INFINITY;
+    int idx = 0x7fffffff;
+    for (int i = threadIdx.x; i < dp.np; i += blockDim.x) {
+        const double s = dq.sde[i];
+        if (s > v) {
+            v = s;
+            idx = i;
+        }
+    }
+    bv[threadIdx.x] = v;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double ov = bv[threadIdx.x + s];
+            const int oi = bi[threadIdx.x + s];
+            if (ov > bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                bv[threadIdx.x] = ov;
+                bi[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int b = bi[0];
+        gtls_result r;
+        const int j = dq.dur[b];
+        r.period = dp.periods[b];
+        r.duration_days = dp.q[j] * dp.periods[b];
+        r.t0 = dq.t0[b];
+        r.depth = dq.depth[b];
+        r.sde = dq.sde[b];
+        r.chi2 = dq.chi2[b];
+        r.chi2_min = dq.stats[0];
+        r.chi2_0 = dc.scal[1];
+        r.period_idx = b;
+        r.dur_idx = j;
+        r.dur_points = dp.dpts[j];
+        r.t0_idx = dq.t0i[b];
+        r.uniform_dy = dc.scal[2] > 0.0 ? 1 : 0;
+        r.reserved0 = 0;
+        *dq.result = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <class T>
+gtls_status dev_alloc(gtls_plan* pl, T** ptr, size_t count)
+{
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    if (pl->n_allocs >= (int)(sizeof(pl->allocs) / sizeof(pl->allocs[0])))
+        return fail(GTLS_ERR_INTERNAL, "too many plan allocations");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(GTLS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    pl->allocs[pl->n_allocs++] = p;
+    pl->device_bytes += (int64_t)(count * sizeof(T));
+    *ptr = static_cast<T*>(p);
+    return GTLS_OK;
+}
+
+template <class T>
+gtls_status upload(gtls_plan* pl, T** ptr, const std::vector<T>& v)
+{
+    gtls_status s = dev_alloc(pl, ptr, v.size());
+    if (s != GTLS_OK) return s;
+    if (!v.empty()) GTLS_CUDA(cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return GTLS_OK;
+}
+
+#define GTLS_TRY(x)                     \
+    do {                                \
+        gtls_status s_ = (x);           \
+        if (s_ != GTLS_OK) return s_;   \
+    } while (0)
+
+int fold_smem_bytes(int bucket_log2)
+{
+    return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long);
+}
+
+gtls_status create_device(gtls_plan* pl)
+{
+    const PlanHost& h = pl->host;
+    GTLS_CUDA(cudaGetDevice(&pl->device));
+    DevPlan& dp = pl->dp;
+    dp.n = h.n;
+    dp.np = (int32_t)h.periods.size();
+    dp.nd = (int32_t)h.q.size();
+    dp.time_exponent = h.time_exponent;
+    dp.idx_bits = h.idx_bits;
+    dp.bucket_log2 = h.bucket_log2;
+    dp.max_kept = h.max_kept;
+    std::vector<float> inv_sum_t(dp.nd), sum_t2f(dp.nd);
+    for (int j = 0; j < dp.nd; ++j) {
+        inv_sum_t[j] = (float)(1.0 / h.sum_t[j]);
+        sum_t2f[j] = (float)h.sum_t2[j];
+    }
+    GTLS_TRY(upload(pl, const_cast<double**>(&dp.periods), h.periods));
+    GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.p_lat), h.p_lat));
+    GTLS_TRY(upload(pl, const_cast<float**>(&dp.inv_p), h.inv_p));
+    GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.bucket_shift), h.bucket_shift));
+    GTLS_TRY(upload(pl, const_cast<uint32_t**>(&dp.bucket_mul), h.bucket_mul));
+    GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.jlo), h.jlo));
+    GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.jhi), h.jhi));
+    GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.dmax_p), h.dmax_p));
+    GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.dpts), h.dpts));
+    GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.stride), h.stride));
+    GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl_off), h.tmpl_off));
+    GTLS_TRY(upload(pl, const_cast<float**>(&dp.tmpl), h.tmpl));
+    GTLS_TRY(upload(pl, const_cast<float**>(&dp.inv_sum_t), inv_sum_t));
+    GTLS_TRY(upload(pl, const_cast<float**>(&dp.sum_t2), sum_t2f));
+    GTLS_TRY(upload(pl, const_cast<double**>(&dp.sum_t), h.sum_t));
+    GTLS_TRY(upload(pl, const_cast<double**>(&dp.q), h.q));
+
+    const int64_t n = h.n;
+    DevCurve& dc = pl->dc;
+    GTLS_TRY(dev_alloc(pl, &dc.d_lat, n));
+    GTLS_TRY(dev_alloc(pl, &dc.d_f, n));
+    GTLS_TRY(dev_alloc(pl, &dc.r32, n));
+    GTLS_TRY(dev_alloc(pl, &dc.rfx, n));
+    GTLS_TRY(dev_alloc(pl, &dc.w32, n));
+    GTLS_TRY(dev_alloc(pl, &dc.scal, 8));
+    GTLS_TRY(dev_alloc(pl, &dc.tmin_key, 1));
+    GTLS_TRY(dev_alloc(pl, &dc.flags, 1));
+    GTLS_TRY(dev_alloc(pl, &dc.part, 1024));
+
+    DevChunk& dk = pl->dk;
+    dk.fold_stride = (n + 31) & ~int64_t(31);
+    dk.pad_stride = (n + h.dmax + kPadMargin + 31) & ~int64_t(31);
+    const int64_t per_period = dk.fold_stride * (8 + 4 + 4) + dk.pad_stride * (4 + 4 + 4 + 8);
+    const int64_t budget = int64_t(1) << 31;  // 2 GiB of chunk scratch
+    int64_t chunk = std::max<int64_t>(1, budget / per_period);
+    chunk = std::min<int64_t>(chunk, 1024);
+    chunk = std::min<int64_t>(chunk, dp.np);
+    dk.chunk = (int32_t)chunk;
+    GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.slot, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.sidx, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.rs, chunk * dk.pad_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.ws, chunk * dk.pad_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.wrs, chunk * dk.pad_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.pf, chunk * dk.pad_stride));
+
+    DevPeriod& dq = pl->dq;
+    const int64_t np_ = dp.np;
+    GTLS_TRY(dev_alloc(pl, &dq.best, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.chi2, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.dur, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.t0i, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.depth, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.t0, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.sr, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.sde_raw, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.sde, np_));
+    GTLS_TRY(dev_alloc(pl, &dq.stats, 4));
+    GTLS_TRY(dev_alloc(pl, &dq.result, 1));
+
+    GTLS_CUDA(cudaFuncSetAttribute(k_fold_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   fold_smem_bytes(h.bucket_log2)));
+    GTLS_CUDA(cudaFuncSetAttribute(k_median_sde, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kMedianCap * (int)(sizeof(double) + sizeof(int))));
+    return GTLS_OK;
+}
+
+enum Stage { kStagePrepare = 0, kStageFold, kStageWindow, kStageFinalize, kStageSrSde, kStageCount };
+
+// Record the end of a stage interval on the search stream (profiling only).
+gtls_status mark(gtls_plan* pl, cudaStream_t st, int stage, size_t& used)
+{
+    if (!pl->profiling) return GTLS_OK;
+    if (used == pl->events.size()) {
+        cudaEvent_t e;
+        GTLS_CUDA(cudaEventCreate(&e));
+        pl->events.push_back(e);
+        pl->event_stage.push_back(stage);
+    }
+    pl->event_stage[used] = stage;
+    GTLS_CUDA(cudaEventRecord(pl->events[used], st));
+    ++used;
+    return GTLS_OK;
+}
+
+gtls_status collect_profile(gtls_plan* pl, size_t used)
+{
+    double ms[kStageCount] = {0, 0, 0, 0, 0};
+    for (size_t i = 1; i < used; ++i) {
+        float dt = 0.0f;
+        GTLS_CUDA(cudaEventElapsedTime(&dt, pl->events[i - 1], pl->events[i]));
+        const int sg = pl->event_stage[i];
+        if (sg >= 0 && sg < kStageCount) ms[sg] += dt;
+    }
+    pl->profile.ms_prepare = ms[kStagePrepare];
+    pl->profile.ms_fold_sort = ms[kStageFold];
+    pl->profile.ms_window_search = ms[kStageWindow];
+    pl->profile.ms_finalize = ms[kStageFinalize];
+    pl->profile.ms_sr_sde = ms[kStageSrSde];
+    pl->profile.enabled = 1;
+    return GTLS_OK;
+}
+
+gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const double* dy,
+                       int64_t n, cudaStream_t st, gtls_result* out,
+                       const gtls_period_outputs* per)
+{
+    const PlanHost& h = pl->host;
+    if (n != h.n)
+        return fail(GTLS_ERR_INVALID_ARG, "n (" + std::to_string(n) + ") differs from the plan's n_points (" +
+                                              std::to_string(h.n) + ")");
+    if (!t || !y || !dy || !out) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    int dev = -1;
+    GTLS_CUDA(cudaGetDevice(&dev));
+    if (dev != pl->device) return fail(GTLS_ERR_INVALID_ARG, "current device differs from the plan's device");
+
+    DevPlan dp = pl->dp;
+    DevCurve dc = pl->dc;
+    DevChunk dk = pl->dk;
+    DevPeriod dq = pl->dq;
+
+    pl->profile = gtls_profile{};
+    size_t ev = 0;
+    int64_t launches = 0, window_launches = 0;
+    GTLS_TRY(mark(pl, st, -1, ev));
+    GTLS_CUDA(cudaMemsetAsync(dc.tmin_key, 0xff, sizeof(unsigned long long), st));
+    GTLS_CUDA(cudaMemsetAsync(dc.flags, 0, sizeof(unsigned int), st));
+    const int prep_blocks = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    k_curve_minmax<<<prep_blocks, 256, 0, st>>>(t, y, dy, n, dc);
+    GTLS_CUDA(cudaGetLastError());
+    k_curve_prep<<<prep_blocks, 256, 0, st>>>(t, y, dy, n, dp.time_exponent, dc);
+    GTLS_CUDA(cudaGetLastError());
+    k_curve_reduce<<<1, 32, 0, st>>>(prep_blocks, dy, dc);
+    GTLS_CUDA(cudaGetLastError());
+    launches += 3;
+    GTLS_TRY(mark(pl, st, kStagePrepare, ev));
+    unsigned int flags = 0;
+    GTLS_CUDA(cudaMemcpyAsync(&flags, dc.flags, sizeof flags, cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaStreamSynchronize(st));
+    if (flags & 1u) return fail(GTLS_ERR_INVALID_ARG, "t, y or dy holds a NaN or infinity");
+    if (flags & 2u) return fail(GTLS_ERR_INVALID_ARG, "dy must be > 0 everywhere");
+
+    const int fold_smem = fold_smem_bytes(h.bucket_log2);
+    const int64_t max_win = n;  // stride >= 1
+    for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
+        const int cnt = std::min<int>(dk.chunk, dp.np - p0);
+        k_fold_sort<<<cnt, kFoldThreads, fold_smem, st>>>(dp, dc, dk, dq, p0);
+        GTLS_CUDA(cudaGetLastError());
+        GTLS_TRY(mark(pl, st, kStageFold, ev));
+        dim3 grid((unsigned)((max_win + kSearchThreads - 1) / kSearchThreads), (unsigned)h.max_kept,
+                  (unsigned)cnt);
+        k_window_search<<<grid, kSearchThreads, 0, st>>>(dp, dc, dk, dq, p0);
+        GTLS_CUDA(cudaGetLastError());
+        GTLS_TRY(mark(pl, st, kStageWindow, ev));
+        k_period_finalize<<<(cnt + 127) / 128, 128, 0, st>>>(dp, dc, dk, dq, p0, cnt);
+        GTLS_CUDA(cudaGetLastError());
+        GTLS_TRY(mark(pl, st, kStageFinalize, ev));
+        launches += 3;
+        window_launches += 1;
+    }
+    k_sr_stats<<<1, 1024, 0, st>>>(dp.np, dq);
+    GTLS_CUDA(cudaGetLastError());
+    const int hwin = h.median_window / 2;
+    const int outs = std::min(1024, kMedianCap - 2 * hwin) & ~31;
+    if (outs < 32) return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
+    k_median_sde<<<(dp.np + outs - 1) / outs, kMedianThreads,
+                   kMedianCap * (int)(sizeof(double) + sizeof(int)), st>>>(dp.np, hwin, outs, dq);
+    GTLS_CUDA(cudaGetLastError());
+    k_best<<<1, 1024, 0, st>>>(dp, dc, dq);
+    GTLS_CUDA(cudaGetLastError());
+    launches += 3;
+    GTLS_TRY(mark(pl, st, kStageSrSde, ev));
+    if (per) {
+        const size_t np_ = (size_t)dp.np;
+        if (per->chi2) GTLS_CUDA(cudaMemcpyAsync(per->chi2, dq.chi2, np_ * 8, cudaMemcpyDeviceToDevice, st));
+        if (per->dur_idx) GTLS_CUDA(cudaMemcpyAsync(per->dur_idx, dq.dur, np_ * 4, cudaMemcpyDeviceToDevice, st));
+        if (per->t0_idx) GTLS_CUDA(cudaMemcpyAsync(per->t0_idx, dq.t0i, np_ * 4, cudaMemcpyDeviceToDevice, st));
+        if (per->depth) GTLS_CUDA(cudaMemcpyAsync(per->depth, dq.depth, np_ * 8, cudaMemcpyDeviceToDevice, st));
+        if (per->t0) GTLS_CUDA(cudaMemcpyAsync(per->t0, dq.t0, np_ * 8, cudaMemcpyDeviceToDevice, st));
+        if (per->sr) GTLS_CUDA(cudaMemcpyAsync(per->sr, dq.sr, np_ * 8, cudaMemcpyDeviceToDevice, st));
+        if (per->sde_raw) GTLS_CUDA(cudaMemcpyAsync(per->sde_raw, dq.sde_raw, np_ * 8, cudaMemcpyDeviceToDevice, st));
+        if (per->sde) GTLS_CUDA(cudaMemcpyAsync(per->sde, dq.sde, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    GTLS_CUDA(cudaMemcpyAsync(out, dq.result, sizeof(gtls_result), cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaStreamSynchronize(st));
+    pl->profile.kernel_launches = launches;
+    pl->profile.window_search_launches = window_launches;
+    if (pl->profiling) GTLS_TRY(collect_profile(pl, ev));
+    return GTLS_OK;
+}
+
+void release(gtls_plan* pl)
+{
+    if (!pl) return;
+    for (cudaEvent_t e : pl->events) cudaEventDestroy(e);
+    pl->events.clear();
+    for (int i = 0; i < pl->n_allocs; ++i) cudaFree(pl->allocs[i]);
+    pl->n_allocs = 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void gtls_plan_params_default(gtls_plan_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->m_star = 1.0;
+    p->r_star = 1.0;
+    p->oversampling = 3.0;
+    p->k_min = 20.05;
+    p->k_max = 620.84;
+    p->q_cap = 0.15;
+    p->dur_ratio = 1.1;
+    p->dt0 = 0.05;
+    p->u1 = 0.4;
+    p->u2 = 0.25;
+}
+
+gtls_status gtls_plan_create(const gtls_plan_params* p, gtls_plan** out)
+{
+    if (!p || !out) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    *out = nullptr;
+    gtls_plan* pl = new (std::nothrow) gtls_plan();
+    if (!pl) return fail(GTLS_ERR_OOM, "host allocation of the plan failed");
+    std::string err;
+    try {
+        if (!build_plan_host(*p, pl->host, err)) {
+            delete pl;
+            return fail(GTLS_ERR_INVALID_ARG, err);
+        }
+    } catch (const std::bad_alloc&) {
+        delete pl;
+        return fail(GTLS_ERR_OOM, "host allocation failed while building the grids");
+    }
+    gtls_status s = create_device(pl);
+    if (s != GTLS_OK) {
+        release(pl);
+        delete pl;
+        return s;
+    }
+    *out = pl;
+    return GTLS_OK;
+}
+
+gtls_status gtls_plan_get_info(const gtls_plan* pl, gtls_plan_info* o)
+{
+    if (!pl || !o) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    const PlanHost& h = pl->host;
+    o->n_periods = (int64_t)h.periods.size();
+    o->n_points = h.n;
+    o->n_durations = (int32_t)h.q.size();
+    o->time_exponent = h.time_exponent;
+    o->max_duration_points = h.dmax;
+    o->n_windows = h.n_windows;
+    o->wpe = h.wpe;
+    o->device_bytes = pl->device_bytes;
+    o->median_window = h.median_window;
+    o->periods_per_chunk = pl->dk.chunk;
+    return GTLS_OK;
+}
+
+gtls_status gtls_plan_get_periods(const gtls_plan* pl, double* o)
+{
+    if (!pl || !o) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    std::memcpy(o, pl->host.periods.data(), pl->host.periods.size() * sizeof(double));
+    return GTLS_OK;
+}
+
+gtls_status gtls_plan_get_durations(const gtls_plan* pl, double* q, int32_t* pts)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    if (q) std::memcpy(q, pl->host.q.data(), pl->host.q.size() * sizeof(double));
+    if (pts) std::memcpy(pts, pl->host.dpts.data(), pl->host.dpts.size() * sizeof(int32_t));
+    return GTLS_OK;
+}
+
+gtls_status gtls_plan_get_ranges(const gtls_plan* pl, int32_t* jlo, int32_t* jhi)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    if (jlo) std::memcpy(jlo, pl->host.jlo.data(), pl->host.jlo.size() * sizeof(int32_t));
+    if (jhi) std::memcpy(jhi, pl->host.jhi.data(), pl->host.jhi.size() * sizeof(int32_t));
+    return GTLS_OK;
+}
+
+gtls_status gtls_search(gtls_plan* pl, const double* t, const double* y, const double* dy,
+                        int64_t n, void* stream, gtls_result* out, const gtls_period_outputs* per)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    g_last_error.clear();
+    return run_search(pl, t, y, dy, n, static_cast<cudaStream_t>(stream), out, per);
+}
+
+gtls_status gtls_search_host(gtls_plan* pl, const double* t, const double* y, const double* dy,
+                             int64_t n, void* stream, gtls_result* out)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    if (!t || !y || !dy || !out) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    if (n != pl->host.n) return fail(GTLS_ERR_INVALID_ARG, "n differs from the plan's n_points");
+    g_last_error.clear();
+    if (!pl->in_t) {
+        GTLS_TRY(dev_alloc(pl, &pl->in_t, n));
+        GTLS_TRY(dev_alloc(pl, &pl->in_y, n));
+        GTLS_TRY(dev_alloc(pl, &pl->in_dy, n));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GTLS_CUDA(cudaMemcpyAsync(pl->in_t, t, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    GTLS_CUDA(cudaMemcpyAsync(pl->in_y, y, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    GTLS_CUDA(cudaMemcpyAsync(pl->in_dy, dy, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    return run_search(pl, pl->in_t, pl->in_y, pl->in_dy, n, st, out, nullptr);
+}
+
+gtls_status gtls_search_batch(gtls_plan* const* plans, int64_t n_lc, const double* t, const double* y,
+                              const double* dy, const int64_t* offsets, void* stream, gtls_result* out)
+{
+    if (!plans || !offsets || !out || n_lc < 0) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    g_last_error.clear();
+    for (int64_t i = 0; i < n_lc; ++i) {
+        const int64_t a = offsets[i], b = offsets[i + 1];
+        if (b < a) return fail(GTLS_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        gtls_status s = run_search(plans[i], t + a, y + a, dy + a, b - a,
+                                   static_cast<cudaStream_t>(stream), &out[i], nullptr);
+        if (s != GTLS_OK) return fail(s, "light curve " + std::to_string(i) + ": " + g_last_error);
+    }
+    return GTLS_OK;
+}
+
+void gtls_plan_destroy(gtls_plan* pl)
+{
+    if (!pl) return;
+    int cur = -1;
+    const bool switch_dev = cudaGetDevice(&cur) == cudaSuccess && cur != pl->device && pl->device >= 0;
+    if (switch_dev) cudaSetDevice(pl->device);
+    release(pl);
+    if (switch_dev) cudaSetDevice(cur);
+    delete pl;
+}
+
+gtls_status gtls_plan_set_profiling(gtls_plan* pl, int32_t on)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    pl->profiling = on != 0;
+    return GTLS_OK;
+}
+
+gtls_status gtls_plan_get_profile(const gtls_plan* pl, gtls_profile* out)
+{
+    if (!pl || !out) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    *out = pl->profile;
+    return GTLS_OK;
+}
+
+const char* gtls_last_error(void) { return g_last_error.c_str(); }
+
+const char* gtls_status_string(gtls_status s)
+{
+    switch (s) {
+    case GTLS_OK: return "GTLS_OK";
+    case GTLS_ERR_INVALID_ARG: return "GTLS_ERR_INVALID_ARG";
+    case GTLS_ERR_CUDA: return "GTLS_ERR_CUDA";
+    case GTLS_ERR_OOM: return "GTLS_ERR_OOM";
+    case GTLS_ERR_TIMEOUT: return "GTLS_ERR_TIMEOUT";
+    case GTLS_ERR_INTERNAL: return "GTLS_ERR_INTERNAL";
+    }
+    return "GTLS_UNKNOWN";
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+"""ctypes binding of libgtls (argument marshalling only).
+
+The names follow the C ABI in ``include/gtls.h``: ``gtls_plan_create``,
+``gtls_search``, ``gtls_search_host``, ``gtls_search_batch``,
+``gtls_plan_destroy``.  Every step of the search runs in the library's CUDA
+kernels; this module never computes any part of it.  Loading fails loudly
+when the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_int64_p = ctypes.POINTER(ctypes.c_int64)
+
+STATUS = {0: "GTLS_OK", 1: "GTLS_ERR_INVALID_ARG", 2: "GTLS_ERR_CUDA", 3: "GTLS_ERR_OOM",
+          4: "GTLS_ERR_TIMEOUT", 5: "GTLS_ERR_INTERNAL"}
+
+
+class GtlsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("baseline_days", ctypes.c_double), ("n_points", ctypes.c_int64),
+                ("m_star", ctypes.c_double), ("r_star", ctypes.c_double),
+                ("oversampling", ctypes.c_double), ("period_min_days", ctypes.c_double),
+                ("period_max_days", ctypes.c_double), ("k_min", ctypes.c_double),
+                ("k_max", ctypes.c_double), ("q_cap", ctypes.c_double),
+                ("dur_ratio", ctypes.c_double), ("dt0", ctypes.c_double),
+                ("u1", ctypes.c_double), ("u2", ctypes.c_double),
+                ("median_window", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("periods_days", c_double_p), ("n_periods", ctypes.c_int64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_periods", ctypes.c_int64), ("n_points", ctypes.c_int64),
+                ("n_durations", ctypes.c_int32), ("time_exponent", ctypes.c_int32),
+                ("max_duration_points", ctypes.c_int64), ("n_windows", ctypes.c_int64),
+                ("wpe", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("median_window", ctypes.c_int32), ("periods_per_chunk", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("period", ctypes.c_double), ("duration_days", ctypes.c_double),
+                ("t0", ctypes.c_double), ("depth", ctypes.c_double), ("sde", ctypes.c_double),
+                ("chi2", ctypes.c_double), ("chi2_min", ctypes.c_double),
+                ("chi2_0", ctypes.c_double), ("period_idx", ctypes.c_int64),
+                ("dur_idx", ctypes.c_int32), ("dur_points", ctypes.c_int32),
+                ("t0_idx", ctypes.c_int64), ("uniform_dy", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms_prepare", ctypes.c_double), ("ms_fold_sort", ctypes.c_double),
+                ("ms_window_search", ctypes.c_double), ("ms_finalize", ctypes.c_double),
+                ("ms_sr_sde", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("window_search_launches", ctypes.c_int64), ("enabled", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
+class PeriodOutputs(ctypes.Structure):
+    _fields_ = [("chi2", ctypes.c_void_p), ("dur_idx", ctypes.c_void_p),
+                ("t0_idx", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("t0", ctypes.c_void_p), ("sr", ctypes.c_void_p),
+                ("sde_raw", ctypes.c_void_p), ("sde", ctypes.c_void_p)]
+
+
+# (name, restype, argtypes) of every symbol declared in include/gtls.h
+SIGNATURES = [
+    ("gtls_plan_params_default", None, [ctypes.POINTER(PlanParams)]),
+    ("gtls_plan_create", ctypes.c_int, [ctypes.POINTER(PlanParams), ctypes.POINTER(ctypes.c_void_p)]),
+    ("gtls_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    ("gtls_plan_get_periods", ctypes.c_int, [ctypes.c_void_p, c_double_p]),
+    ("gtls_plan_get_durations", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_int32_p]),
+    ("gtls_plan_get_ranges", ctypes.c_int, [ctypes.c_void_p, c_int32_p, c_int32_p]),
+    ("gtls_search", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.POINTER(Result), ctypes.POINTER(PeriodOutputs)]),
+    ("gtls_search_host", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(Result)]),
+    ("gtls_search_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         c_int64_p, ctypes.c_void_p, ctypes.POINTER(Result)]),
+    ("gtls_plan_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("gtls_plan_get_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
+    ("gtls_plan_destroy", None, [ctypes.c_void_p]),
+    ("gtls_last_error", ctypes.c_char_p, []),
+    ("gtls_status_string", ctypes.c_char_p, [ctypes.c_int]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgtls.so (building it first if allowed).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or not _build.up_to_date():
+                if not build_if_missing:
+                    raise RuntimeError(f"libgtls.so is not built ({path})")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise GtlsError(status, _lib.gtls_last_error().decode())
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int address)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclasses.dataclass
+class PlanConfig:
+    baseline_days: float
+    n_points: int
+    m_star: float = 1.0
+    r_star: float = 1.0
+    oversampling: float = 3.0
+    period_min_days: float = 0.0
+    period_max_days: float = 0.0
+    k_min: float = 20.05
+    k_max: float = 620.84
+    q_cap: float = 0.15
+    dur_ratio: float = 1.1
+    dt0: float = 0.05
+    u1: float = 0.4
+    u2: float = 0.25
+    median_window: int = 0
+    periods_days: np.ndarray | None = None
+
+
+class Plan:
+    """Owner of a gtls_plan (grids, templates and device scratch)."""
+
+    def __init__(self, cfg: PlanConfig):
+        lib = load()
+        prm = PlanParams()
+        lib.gtls_plan_params_default(ctypes.byref(prm))
+        for f in ("baseline_days", "n_points", "m_star", "r_star", "oversampling",
+                  "period_min_days", "period_max_days", "k_min", "k_max", "q_cap",
+                  "dur_ratio", "dt0", "u1", "u2", "median_window"):
+            v = getattr(cfg, f)
+            setattr(prm, f, v if v is not None else 0)
+        self._periods_in = None
+        if cfg.periods_days is not None:
+            self._periods_in = np.ascontiguousarray(cfg.periods_days, dtype=np.float64)
+            prm.periods_days = self._periods_in.ctypes.data_as(c_double_p)
+            prm.n_periods = self._periods_in.size
+        h = ctypes.c_void_p()
+        _check(lib.gtls_plan_create(ctypes.byref(prm), ctypes.byref(h)))
+        self.handle = h
+        self.cfg = cfg
+        info = PlanInfo()
+        _check(lib.gtls_plan_get_info(self.handle, ctypes.byref(info)))
+        self.info = info
+
+    # -- grids --------------------------------------------------------------
+    @property
+    def n_periods(self) -> int:
+        return int(self.info.n_periods)
+
+    def periods(self) -> np.ndarray:
+        out = np.empty(self.n_periods)
+        _check(_lib.gtls_plan_get_periods(self.handle, out.ctypes.data_as(c_double_p)))
+        return out
+
+    def durations(self):
+        nd = int(self.info.n_durations)
+        q = np.empty(nd)
+        d = np.empty(nd, np.int32)
+        _check(_lib.gtls_plan_get_durations(self.handle, q.ctypes.data_as(c_double_p),
+                                            d.ctypes.data_as(c_int32_p)))
+        return q, d
+
+    def ranges(self):
+        lo = np.empty(self.n_periods, np.int32)
+        hi = np.empty(self.n_periods, np.int32)
+        _check(_lib.gtls_plan_get_ranges(self.handle, lo.ctypes.data_as(c_int32_p),
+                                         hi.ctypes.data_as(c_int32_p)))
+        return lo, hi
+
+    # -- searches -----------------------------------------------------------
+    def search(self, t, y, dy, stream=None, per_period=None) -> Result:
+        """gtls_search on device tensors (float64, contiguous, same device)."""
+        res = Result()
+        po = None
+        if per_period is not None:
+            po = PeriodOutputs(*[_ptr(per_period.get(f)) for f, _ in PeriodOutputs._fields_])
+        n = int(t.numel()) if hasattr(t, "numel") else int(len(t))
+        _check(_lib.gtls_search(self.handle, _ptr(t), _ptr(y), _ptr(dy), n,
+                                _stream_handle(stream), ctypes.byref(res),
+                                ctypes.byref(po) if po is not None else None))
+        return res
+
+    def search_host(self, t, y, dy, stream=None) -> Result:
+        """gtls_search_host on host float64 arrays (copies to the device inside)."""
+        t = np.ascontiguousarray(t, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        dy = np.ascontiguousarray(dy, np.float64)
+        res = Result()
+        _check(_lib.gtls_search_host(self.handle, t.ctypes.data_as(c_double_p),
+                                     y.ctypes.data_as(c_double_p), dy.ctypes.data_as(c_double_p),
+                                     t.size, _stream_handle(stream), ctypes.byref(res)))
+        return res
+
+    def set_profiling(self, on: bool = True):
+        _check(_lib.gtls_plan_set_profiling(self.handle, 1 if on else 0))
+
+    def profile(self) -> Profile:
+        pr = Profile()
+        _check(_lib.gtls_plan_get_profile(self.handle, ctypes.byref(pr)))
+        return pr
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.gtls_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def search_batch(plans, t, y, dy, offsets, stream=None):
+    """gtls_search_batch: CSR-packed device tensors, one plan per curve."""
+    lib = load()
+    n_lc = len(plans)
+    arr = (ctypes.c_void_p * n_lc)(*[p.handle.value for p in plans])
+    offs = np.ascontiguousarray(offsets, np.int64)
+    out = (Result * n_lc)()
+    _check(lib.gtls_search_batch(arr, n_lc, _ptr(t), _ptr(y), _ptr(dy),
+                                 offs.ctypes.data_as(c_int64_p), _stream_handle(stream), out))
+    return list(out)

@@ -1,0 +1,219 @@
+"""GPU parity of libgtls against the FP64 oracle, through the C ABI.
+
+Tolerances (stated for the FP32 window sums of the kernels):
+  * grid arrays, duration ranges, best period / duration / T0 indices: exact;
+  * chi2(P): 1e-5 relative; SDE: 1e-3 absolute;
+  * per-period argmin (duration, T0 start): exact, or -- where FP32 rounding
+    picks a different window of a near tie -- the oracle's chi2 of the GPU's
+    window lies within 1e-5 relative of the oracle's minimum.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import grid
+from oracle import search as osr
+
+from . import gpu_helpers as gh
+
+pytestmark = pytest.mark.gpu
+
+CHI2_RTOL = 1e-5
+SDE_ATOL = 1e-3
+
+
+def _check_argmins(op, t, y, dy, r_or, out, periods_idx=None):
+    """Exact argmin or a valid near-tie alternative; returns #exact."""
+    sel = r_or.sel if periods_idx is None else periods_idx
+    exact = 0
+    for k, p in enumerate(sel):
+        jg, sg = int(out["dur_idx"][p]), int(out["t0_idx"][p])
+        if (jg, sg) == (int(r_or.j_best[k]), int(r_or.s_best[k])):
+            exact += 1
+            continue
+        c, _ = osr.period_windows(op, t, y, dy, int(p), jg)
+        st = grid.t0_stride(int(op.dur_pts[jg]), op.dt0)
+        assert sg % st == 0
+        alt = c[sg // st]
+        assert alt == pytest.approx(r_or.chi2[k], rel=CHI2_RTOL), (p, jg, sg)
+    return exact
+
+
+@pytest.mark.parametrize("name", ["short_white", "kepler_like", "long_baseline"])
+def test_grids_match_oracle(name):
+    lc = synth.make_workload(name)
+    cfg = lc.search
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    per = pl.periods()
+    assert per.size == op.periods.size
+    np.testing.assert_allclose(per, op.periods, rtol=1e-13, atol=0)
+    q, d = pl.durations()
+    np.testing.assert_allclose(q, op.q, rtol=1e-13, atol=0)
+    assert np.array_equal(d, op.dur_pts)
+    lo, hi = pl.ranges()
+    assert np.array_equal(lo, op.jlo) and np.array_equal(hi, op.jhi)
+    assert pl.info.time_exponent == op.e
+    pl.close()
+
+
+def test_short_white_full_grid_parity():
+    lc = synth.short_white()
+    cfg = lc.search
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, lc.t, lc.y, lc.dy)
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    exact = _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out)
+    assert exact >= 0.99 * r_or.sel.size
+    np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
+    np.testing.assert_allclose(out["sr"], sr_or, rtol=CHI2_RTOL, atol=0)
+    assert res.period_idx == best_or["period_idx"]
+    assert res.dur_idx == best_or["dur_idx"]
+    assert res.t0_idx == best_or["t0_idx"]
+    assert res.t0 == best_or["t0"]
+    assert res.sde == pytest.approx(best_or["sde"], abs=SDE_ATOL)
+    assert res.chi2 == pytest.approx(best_or["chi2"], rel=CHI2_RTOL)
+    assert res.depth == pytest.approx(best_or["depth"], rel=1e-6)
+    assert res.chi2_0 == pytest.approx(best_or["chi2_0"], rel=1e-12)
+    assert res.uniform_dy == 1
+    pl.close()
+
+
+@pytest.mark.parametrize("n,seed", [(5, 0), (97, 1), (1001, 2)])
+def test_per_point_weights_and_ragged_sizes(n, seed):
+    rng = np.random.default_rng(seed)
+    t = np.sort(rng.uniform(0.0, 40.0, n))
+    y = 1.0 + rng.normal(0, 1e-3, n)
+    y[rng.random(n) < 0.05] -= 4e-3
+    dy = rng.uniform(5e-4, 3e-3, n)
+    cfg = dict(period_min_days=0.6, period_max_days=12.0)
+    base = float(t.max() - t.min())
+    op = gh.oracle_plan_for(n, base, cfg)
+    r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, t, y, dy)
+    pl = gh.plan_for(n, base, cfg)
+    res, out = gh.gpu_search(pl, t, y, dy)
+    assert res.uniform_dy == 0
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, t, y, dy, r_or, out)
+    np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
+    assert res.period_idx == best_or["period_idx"]
+    pl.close()
+
+
+def test_exact_recovery_of_template_injection():
+    n, a, pstar = 211, 37, 2.345678901
+    t = synth.noiseless_one_point_per_cycle(pstar, n, a)
+    periods = pstar * np.array([0.999, 0.9995, 0.9999, 1.0, 1.0001, 1.0005, 1.001])
+    base = float(t.max() - t.min())
+    op = gh.oracle_plan_for(n, base, periods_days=periods)
+    k = 3
+    js = grid.kept_durations(op.dur_pts, op.jlo[k], op.jhi[k])
+    j = js[len(js) // 2]
+    d = int(op.dur_pts[j])
+    st = grid.t0_stride(d, op.dt0)
+    s = 5 * st
+    tmpl = grid.template(d)
+    pos = (a * np.arange(n)) % n
+    rel = (pos - s) % n
+    y = np.ones(n)
+    inw = rel < d
+    y[inw] = 1.0 - 2.5e-3 * tmpl[rel[inw]]
+    dy = np.full(n, 1e-3)
+    pl = gh.plan_for(n, base, periods_days=periods)
+    res, out = gh.gpu_search(pl, t, y, dy)
+    chi2_0 = float(np.sum(((y - 1) / dy) ** 2))
+    assert out["chi2"][k] <= 1e-5 * chi2_0
+    assert (int(out["dur_idx"][k]), int(out["t0_idx"][k])) == (j, s)
+    assert out["depth"][k] == pytest.approx(2.5e-3, rel=1e-6)
+    assert int(np.argmin(out["chi2"])) == k
+    pl.close()
+
+
+def test_zero_depth_everywhere():
+    rng = np.random.default_rng(11)
+    n = 300
+    t = np.sort(rng.uniform(0, 20, n))
+    y = 1.0 + np.abs(rng.normal(0, 1e-3, n))
+    dy = np.full(n, 1e-3)
+    base = float(t.max() - t.min())
+    pl = gh.plan_for(n, base, period_min_days=0.5, period_max_days=10.0)
+    res, out = gh.gpu_search(pl, t, y, dy)
+    chi2_0 = float(np.sum(((y - 1.0) / dy) ** 2))
+    np.testing.assert_allclose(out["chi2"], chi2_0, rtol=1e-12)
+    assert np.all(out["depth"] == 0.0)
+    assert np.all(out["sr"] == 1.0)
+    assert np.all(out["sde"] == 0.0)
+    pl.close()
+
+
+def test_invalid_inputs_are_reported():
+    import paper_2607_00348_gb300 as pkg
+    lc = synth.short_white()
+    pl = gh.plan_for(lc, lc.baseline_days, lc.search)
+    y = lc.y.copy()
+    y[100] = np.nan
+    with pytest.raises(pkg.GtlsError, match="INVALID_ARG.*NaN"):
+        gh.gpu_search(pl, lc.t, y, lc.dy)
+    dy = lc.dy.copy()
+    dy[7] = 0.0
+    with pytest.raises(pkg.GtlsError, match="INVALID_ARG.*dy"):
+        gh.gpu_search(pl, lc.t, lc.y, dy)
+    with pytest.raises(pkg.GtlsError, match="INVALID_ARG"):
+        gh.gpu_search(pl, lc.t[:-1], lc.y[:-1], lc.dy[:-1])
+    # the plan stays usable after rejected calls
+    res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    assert abs(res.period - 3.7) < 0.05
+    pl.close()
+
+
+def test_host_entry_point_equals_device_entry_point():
+    lc = synth.short_white()
+    pl = gh.plan_for(lc, lc.baseline_days, lc.search)
+    res_d, _ = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    res_h = pl.search_host(lc.t, lc.y, lc.dy)
+    assert res_h.as_dict() == res_d.as_dict()
+    pl.close()
+
+
+def test_batch_equals_single_searches():
+    import torch
+    import paper_2607_00348_gb300 as pkg
+    lcs = [synth.short_white(seed=s) for s in (0, 5, 9)]
+    plans = [gh.plan_for(lc, lc.baseline_days, lc.search) for lc in lcs]
+    singles = [gh.gpu_search(p, lc.t, lc.y, lc.dy)[0].as_dict() for p, lc in zip(plans, lcs)]
+    dev = torch.device("cuda:0")
+    cat = lambda f: torch.as_tensor(np.concatenate([getattr(lc, f) for lc in lcs]),
+                                    dtype=torch.float64, device=dev)
+    offs = np.cumsum([0] + [lc.n for lc in lcs])
+    res = pkg.search_batch(plans, cat("t"), cat("y"), cat("dy"), offs)
+    assert [r.as_dict() for r in res] == singles
+    for p in plans:
+        p.close()
+
+
+def test_kepler_like_full_size_sampled_parity():
+    lc = synth.kepler_like()
+    cfg = lc.search
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    npd = op.periods.size
+    near = int(np.argmin(np.abs(op.periods - lc.injected["period"])))
+    sel = np.unique(np.concatenate([np.arange(0, npd, 4000), np.arange(near - 8, near + 9),
+                                    [npd - 1]]))
+    r_or = osr.search_periods(op, lc.t, lc.y, lc.dy, sel)
+    np.testing.assert_allclose(out["chi2"][sel], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out, sel)
+    # the search finds the injected 37-d transit
+    assert abs(res.period - 37.0) / 37.0 < 2e-3
+    assert res.sde > 9.0
+    # SR / SDE_raw invariants on the full spectrum
+    sr = out["sr"]
+    assert np.all(sr > 0) and np.all(sr <= 1.0)
+    np.testing.assert_allclose(sr * out["chi2"], out["chi2"].min(), rtol=1e-12)
+    assert abs(out["sde_raw"].mean()) < 1e-9
+    assert out["sde_raw"].std() == pytest.approx(1.0, rel=1e-9)
+    pl.close()
