@@ -13,4 +13,4 @@ from .gtls import (  # noqa: F401
     library_path,
     search_batch,
 )
-from .build import build  # noqa: F401
+from .build import build as build_library  # noqa: F401

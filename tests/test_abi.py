@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
 
 
 def test_library_builds_and_exports_every_declared_symbol():
-    path = pkg.build()
+    path = pkg.build_library()
     assert os.path.exists(path)
     lib = ctypes.CDLL(path)
     for name in declared_functions():
