@@ -37,6 +37,7 @@ struct DevPlan {
     const float* sum_t2;      // sum_k s_k^2
     const double* sum_t;      // FP64 sum_k s_k
     const double* q;
+    int64_t tmpl_total;       // floats in tmpl
 };
 
 // Per-light-curve derived arrays (n long unless noted).
@@ -50,6 +51,7 @@ struct DevCurve {
     unsigned long long* tmin_key;  // ordered key of min(t)
     unsigned int* flags;      // bit0 non-finite, bit1 dy <= 0, bit2 dy not uniform
     double* part;             // block partials of chi2_0
+    unsigned int* check;      // [0] first failed device check (0 = none), [1..3] its values
 };
 
 // Per-chunk scratch: `chunk` periods in flight.
@@ -78,6 +80,7 @@ struct DevPeriod {
     double* sde_raw;
     double* sde;
     double* stats;            // [0] chi2_min [1] mean SR [2] std SR
+    unsigned int* check;      // same words as DevCurve::check
     gtls_result* result;      // device copy of the best candidate
 };
 

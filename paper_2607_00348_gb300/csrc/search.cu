@@ -79,6 +79,25 @@ __device__ __forceinline__ float float_from_order_key(unsigned int k)
     return __uint_as_float(u);
 }
 
+// Record the first failed index check of a search; the access is then
+// skipped (or redirected to index 0) so that the kernel never leaves its
+// buffers.  The host turns a recorded check into GTLS_ERR_INTERNAL.
+__device__ __noinline__ void record_check(unsigned int* w, unsigned int code, long long a, long long b)
+{
+    if (atomicCAS(w, 0u, code) == 0u) {
+        w[1] = (unsigned int)a;
+        w[2] = (unsigned int)b;
+        w[3] = (unsigned int)(a >> 32);
+    }
+}
+
+__device__ __forceinline__ bool in_range(unsigned int* w, unsigned int code, long long v, long long hi)
+{
+    if (v >= 0 && v < hi) return true;
+    record_check(w, code, v, hi);
+    return false;
+}
+
 // Exact lattice phase rho = d mod P (0 <= d < 2^62, P > 0).  The float
 // product gives the cycle count to within one; two integer corrections make
 // it exact.
@@ -238,7 +257,7 @@ k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const long long rho = lattice_rho(dc.d_lat[i], dc.d_f[i], P, inv_p);
         const uint32_t b = fold_bucket(rho, sh, mul);
-        slotv[i] = atomicAdd(&hist[b], 1u);
+        slotv[i] = in_range(dc.check, 1, b, nb) && in_range(dc.check, 2, rho, P) ? atomicAdd(&hist[b], 1u) : 0u;
     }
     __syncthreads();
 
@@ -260,7 +279,10 @@ k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const long long rho = lattice_rho(dc.d_lat[i], dc.d_f[i], P, inv_p);
         const uint32_t b = fold_bucket(rho, sh, mul);
-        keys[start[b] + slotv[i]] = ((unsigned long long)rho << ib) | (unsigned long long)i;
+        if (!in_range(dc.check, 3, b, nb)) continue;
+        const long long dst = (long long)start[b] + slotv[i];
+        if (in_range(dc.check, 4, dst, n))
+            keys[dst] = ((unsigned long long)rho << ib) | (unsigned long long)i;
     }
     __syncthreads();
 
@@ -269,11 +291,14 @@ k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
         const unsigned long long key = keys[q];
         const long long rho = (long long)(key >> ib);
         const uint32_t b = fold_bucket(rho, sh, mul);
+        if (!in_range(dc.check, 5, b, nb)) continue;
         const uint32_t lo = start[b], cnt = hist[b];
+        if (!in_range(dc.check, 6, (long long)lo + cnt, n + 1)) continue;
         uint32_t rank = 0;
         for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
         const uint32_t pos = lo + rank;
         const int32_t idx = (int32_t)(key & idx_mask);
+        if (!in_range(dc.check, 7, pos, n) || !in_range(dc.check, 8, idx, n)) continue;
         sidx[pos] = idx;
         rs[pos] = dc.r32[idx];
         pf[pos + 1] = dc.rfx[idx];
@@ -344,7 +369,10 @@ k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
     const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if ((int64_t)blockIdx.x * blockDim.x >= nwin) return;  // whole block past the end
     unsigned long long packed = ~0ull;
-    if (m < nwin) {
+    const bool ok = in_range(dc.check, 9, j, dp.nd) && in_range(dc.check, 10, d, dp.dmax_p[p] + 1) &&
+                    in_range(dc.check, 11, dp.tmpl_off[j] + d, dp.tmpl_total + 1) &&
+                    in_range(dc.check, 12, (nwin - 1) * st + d, dk.pad_stride);
+    if (ok && m < nwin) {
         const int64_t s = m * st;
         const float* rs = dk.rs + (int64_t)slot_id * dk.pad_stride + s;
         const long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
@@ -399,14 +427,17 @@ __global__ void k_period_finalize(DevPlan dp, DevCurve dc, DevChunk dk, DevPerio
     const float dchi = float_from_order_key((unsigned int)(b >> 32));
     const int j = (int)((b >> 24) & 0xffull);
     const int64_t m = (int64_t)(b & 0xffffffull);
+    if (!in_range(dc.check, 13, j, dp.nd)) return;
     const int d = dp.dpts[j], st = dp.stride[j];
     const int64_t s = m * st;
     const int64_t n = dp.n;
+    if (!in_range(dc.check, 14, s + d, dk.pad_stride)) return;
     const long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
     const double sum_r = (double)(pf[s + d] - pf[s]) * (1.0 / kRScale);
     const double depth = fmax(0.0, sum_r / dp.sum_t[j]);
     const int64_t c = (s + d / 2) % n;
     const int32_t idx = dk.sidx[(int64_t)slot_id * dk.fold_stride + c];
+    if (!in_range(dc.check, 15, idx, n)) return;
     const long long rho = lattice_rho(dc.d_lat[idx], dc.d_f[idx], dp.p_lat[p], dp.inv_p[p]);
     dq.chi2[p] = dc.scal[1] + (double)dchi;
     dq.dur[p] = j;
@@ -482,6 +513,10 @@ __global__ void __launch_bounds__(kMedianThreads) k_median_sde(int np, int h, in
     const int lo = max(0, i0 - h);
     const int hi = min(np - 1, i0 + outs - 1 + h);
     const int len = hi - lo + 1;
+    if (len > kMedianCap) {   // block-uniform: the whole block leaves
+        if (threadIdx.x == 0) record_check(dq.check, 16, len, kMedianCap);
+        return;
+    }
     int cap = 1;
     while (cap < len) cap <<= 1;
     for (int k = threadIdx.x; k < cap; k += blockDim.x) {
@@ -564,8 +599,10 @@ __global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPerio
     }
     if (threadIdx.x == 0) {
         const int b = bi[0];
+        if (!in_range(dc.check, 17, b, dp.np)) return;
         gtls_result r;
         const int j = dq.dur[b];
+        if (!in_range(dc.check, 18, j, dp.nd)) return;
         r.period = dp.periods[b];
         r.duration_days = dp.q[j] * dp.periods[b];
         r.t0 = dq.t0[b];
@@ -672,6 +709,8 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(dev_alloc(pl, &dc.tmin_key, 1));
     GTLS_TRY(dev_alloc(pl, &dc.flags, 1));
     GTLS_TRY(dev_alloc(pl, &dc.part, 1024));
+    GTLS_TRY(dev_alloc(pl, &dc.check, 4));
+    dp.tmpl_total = (int64_t)h.tmpl.size();
 
     DevChunk& dk = pl->dk;
     dk.fold_stride = (n + 31) & ~int64_t(31);
@@ -703,6 +742,7 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(dev_alloc(pl, &dq.sde, np_));
     GTLS_TRY(dev_alloc(pl, &dq.stats, 4));
     GTLS_TRY(dev_alloc(pl, &dq.result, 1));
+    dq.check = dc.check;
 
     GTLS_CUDA(cudaFuncSetAttribute(k_fold_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    fold_smem_bytes(h.bucket_log2)));
@@ -771,6 +811,7 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     GTLS_TRY(mark(pl, st, -1, ev));
     GTLS_CUDA(cudaMemsetAsync(dc.tmin_key, 0xff, sizeof(unsigned long long), st));
     GTLS_CUDA(cudaMemsetAsync(dc.flags, 0, sizeof(unsigned int), st));
+    GTLS_CUDA(cudaMemsetAsync(dc.check, 0, 4 * sizeof(unsigned int), st));
     const int prep_blocks = (int)std::min<int64_t>(1024, (n + 255) / 256);
     k_curve_minmax<<<prep_blocks, 256, 0, st>>>(t, y, dy, n, dc);
     GTLS_CUDA(cudaGetLastError());
@@ -827,8 +868,14 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
         if (per->sde_raw) GTLS_CUDA(cudaMemcpyAsync(per->sde_raw, dq.sde_raw, np_ * 8, cudaMemcpyDeviceToDevice, st));
         if (per->sde) GTLS_CUDA(cudaMemcpyAsync(per->sde, dq.sde, np_ * 8, cudaMemcpyDeviceToDevice, st));
     }
+    unsigned int chk[4] = {0, 0, 0, 0};
+    GTLS_CUDA(cudaMemcpyAsync(chk, dc.check, sizeof chk, cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaMemcpyAsync(out, dq.result, sizeof(gtls_result), cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaStreamSynchronize(st));
+    if (chk[0] != 0)
+        return fail(GTLS_ERR_INTERNAL, "device index check " + std::to_string(chk[0]) + " failed (value " +
+                                           std::to_string(((long long)chk[3] << 32) | chk[1]) +
+                                           ", limit " + std::to_string(chk[2]) + ")");
     pl->profile.kernel_launches = launches;
     pl->profile.window_search_launches = window_launches;
     if (pl->profiling) GTLS_TRY(collect_profile(pl, ev));
