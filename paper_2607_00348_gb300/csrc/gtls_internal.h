@@ -97,6 +97,11 @@ struct gtls_plan {
     double* in_y = nullptr;
     double* in_dy = nullptr;
     int64_t device_bytes = 0;
+    // tiled window search (uniform weights)
+    bool tile_ok = false;
+    int tile_buf = 0, tile_len = 0, tile_count = 0;
+    int n_sm = 0;
+    unsigned int* tile_counter = nullptr;
     // stage profiling: events recorded on the search stream when enabled
     bool profiling = false;
     std::vector<cudaEvent_t> events;

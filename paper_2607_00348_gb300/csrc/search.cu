@@ -145,6 +145,12 @@ __device__ long long block_exclusive_scan(long long v, long long* warp_sums, lon
     return out;
 }
 
+}  // namespace
+
+#include "window_tiles.cuh"
+
+namespace {
+
 // ---------------------------------------------------------------------------
 // per-curve preparation
 // ---------------------------------------------------------------------------
@@ -410,6 +416,131 @@ k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
         unsigned long long b = red[0];
         for (int w = 1; w < kSearchThreads / 32; ++w) b = red[w] < b ? red[w] : b;
         atomicMin(&dq.best[p], b);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tiled window search (uniform weights): see window_tiles.cuh
+// ---------------------------------------------------------------------------
+
+struct TileCfg {
+    int buf;     // floats of folded curve staged per item
+    int len;     // window starts per tile (L)
+    int tiles;   // tiles per period
+};
+
+__global__ void __launch_bounds__(tiles::kThreads, 1)
+k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, int p0, int cnt,
+               unsigned int* counter)
+{
+    using namespace tiles;
+    extern __shared__ float tile_smem[];
+    __shared__ DurTask dur[kMaxDur];
+    __shared__ int s_item, s_ndur, s_total, s_task;
+    __shared__ unsigned long long s_best[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int items = cnt * tc.tiles;
+    const float w_uni = (float)dc.scal[2];
+    const int64_t n = dp.n;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= items) break;
+        const int slot = item / tc.tiles, tau = item - (item / tc.tiles) * tc.tiles;
+        const int p = p0 + slot;
+        const int x0 = tau * tc.len;
+
+        // stage the folded, padded curve [x0, x0 + buf) (zeros past its end)
+        const float* src = dk.rs + (int64_t)slot * dk.pad_stride + x0;
+        const int valid = (int)min((int64_t)tc.buf, n + (int64_t)dp.dmax_p[p] + kPadMargin - x0);
+        const int v4 = valid >> 2;
+        for (int i = threadIdx.x; i < v4; i += blockDim.x)
+            reinterpret_cast<float4*>(tile_smem)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
+        for (int i = (v4 << 2) + threadIdx.x; i < tc.buf; i += blockDim.x)
+            tile_smem[i] = i < valid ? src[i] : 0.0f;
+
+        // durations of the period, longest first, with their task ranges
+        if (threadIdx.x == 0) {
+            const int lo = dp.jlo[p], hi = dp.jhi[p];
+            int k = 0, total = 0;
+            for (int j = hi; j >= lo; --j) {
+                if (j > lo && dp.dpts[j] == dp.dpts[j - 1]) continue;
+                if (!in_range(dc.check, 19, k, kMaxDur)) break;
+                DurTask t;
+                t.j = j;
+                t.d = dp.dpts[j];
+                t.st = dp.stride[j];
+                t.m_total = (int)((n + t.st - 1) / t.st);
+                t.m_a = (x0 + t.st - 1) / t.st;
+                t.m_b = min(t.m_total, (x0 + tc.len + t.st - 1) / t.st);
+                const int nwin = max(0, t.m_b - t.m_a);
+                pick_config(t.st, max(1, nwin), t.variant, t.nc);
+                t.w = variant_w(t.variant);
+                t.per_task = 32 * t.w / t.nc;
+                t.tasks = (nwin + t.per_task - 1) / t.per_task;
+                const int jrows = (t.d + t.st - 1) / t.st;
+                const int m_max_start = (x0 + tc.buf) / t.st - t.w - jrows;
+                t.hi_start = min(t.m_total - t.w, m_max_start);
+                if (t.tasks > 0) in_range(dc.check, 20, (int64_t)t.m_a, (int64_t)m_max_start + 1);
+                t.first = total;
+                total += t.tasks;
+                dur[k++] = t;
+            }
+            s_ndur = k;
+            s_total = total;
+            s_task = 0;
+        }
+        __syncthreads();
+
+        unsigned long long best = ~0ull;
+        const int ndur = s_ndur, total = s_total;
+        for (;;) {
+            int task = 0;
+            if (lane == 0) task = atomicAdd(&s_task, 1);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (task >= total) break;
+            int k = 0;
+            while (k + 1 < ndur && dur[k + 1].first <= task) ++k;
+            const DurTask t = dur[k];
+            WinCtx c;
+            c.tile = tile_smem;
+            c.x0 = x0;
+            c.d = t.d;
+            c.st = t.st;
+            c.nc = t.nc;
+            c.lg_nc = __ffs(t.nc) - 1;
+            c.m_first = t.m_a + (task - t.first) * t.per_task;
+            c.m_a = t.m_a;
+            c.m_b = t.m_b;
+            c.hi_start = t.hi_start;
+            c.m_total = t.m_total;
+            c.tg = dp.tmpl + dp.tmpl_off[t.j];
+            c.inv_sum_t = dp.inv_sum_t[t.j];
+            c.sum_t2 = dp.sum_t2[t.j];
+            c.w_uni = w_uni;
+            c.j = t.j;
+            c.pf = dk.pf + (int64_t)slot * dk.pad_stride;
+            switch (t.variant) {
+            case kPair16: warp_task_pair<16>(c, lane, best); break;
+            case kPair14: warp_task_pair<14>(c, lane, best); break;
+            case kPair12: warp_task_pair<12>(c, lane, best); break;
+            case kPair8: warp_task_pair<8>(c, lane, best); break;
+            default: warp_task_scalar<15>(c, lane, best); break;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v < best ? v : best;
+        }
+        if (lane == 0) s_best[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = s_best[0];
+            for (int w = 1; w < kWarps; ++w) b = s_best[w] < b ? s_best[w] : b;
+            atomicMin(&dq.best[p], b);
+        }
     }
 }
 
@@ -744,6 +875,33 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(dev_alloc(pl, &dq.result, 1));
     dq.check = dc.check;
 
+    // tiled window search: staged buffer, tile length, tiles per period
+    {
+        int dev = 0;
+        GTLS_CUDA(cudaGetDevice(&dev));
+        GTLS_CUDA(cudaDeviceGetAttribute(&pl->n_sm, cudaDevAttrMultiProcessorCount, dev));
+        int smem_optin = 0;
+        GTLS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const int static_bytes = 8192;  // duration table and reduction scratch, rounded up
+        const int buf = std::min(55296, (smem_optin - static_bytes) / 4) & ~63;
+        int st_max = 1;
+        bool fits = buf > 0;
+        for (int j = 0; j < dp.nd; ++j) {
+            st_max = std::max(st_max, h.stride[j]);
+            const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
+            if ((int64_t)(16 + jrows + 2) * h.stride[j] > buf) fits = false;
+        }
+        const int64_t len = ((int64_t)buf - h.dmax - 3 * (int64_t)st_max - 64) & ~int64_t(63);
+        pl->tile_ok = fits && len >= 64;
+        if (pl->tile_ok) {
+            pl->tile_buf = buf;
+            pl->tile_len = (int)len;
+            pl->tile_count = (int)((n + len - 1) / len);
+            GTLS_CUDA(cudaFuncSetAttribute(k_window_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           buf * (int)sizeof(float)));
+        }
+        GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
+    }
     GTLS_CUDA(cudaFuncSetAttribute(k_fold_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    fold_smem_bytes(h.bucket_log2)));
     GTLS_CUDA(cudaFuncSetAttribute(k_median_sde, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -828,15 +986,23 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     if (flags & 2u) return fail(GTLS_ERR_INVALID_ARG, "dy must be > 0 everywhere");
 
     const int fold_smem = fold_smem_bytes(h.bucket_log2);
+    const bool use_tiles = pl->tile_ok && !(flags & 4u);
+    TileCfg tc{pl->tile_buf, pl->tile_len, pl->tile_count};
     const int64_t max_win = n;  // stride >= 1
     for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
         const int cnt = std::min<int>(dk.chunk, dp.np - p0);
         k_fold_sort<<<cnt, kFoldThreads, fold_smem, st>>>(dp, dc, dk, dq, p0);
         GTLS_CUDA(cudaGetLastError());
         GTLS_TRY(mark(pl, st, kStageFold, ev));
-        dim3 grid((unsigned)((max_win + kSearchThreads - 1) / kSearchThreads), (unsigned)h.max_kept,
-                  (unsigned)cnt);
-        k_window_search<<<grid, kSearchThreads, 0, st>>>(dp, dc, dk, dq, p0);
+        if (use_tiles) {
+            GTLS_CUDA(cudaMemsetAsync(pl->tile_counter, 0, sizeof(unsigned int), st));
+            k_window_tiles<<<pl->n_sm, tiles::kThreads, pl->tile_buf * (int)sizeof(float), st>>>(
+                dp, dc, dk, dq, tc, p0, cnt, pl->tile_counter);
+        } else {
+            dim3 grid((unsigned)((max_win + kSearchThreads - 1) / kSearchThreads), (unsigned)h.max_kept,
+                      (unsigned)cnt);
+            k_window_search<<<grid, kSearchThreads, 0, st>>>(dp, dc, dk, dq, p0);
+        }
         GTLS_CUDA(cudaGetLastError());
         GTLS_TRY(mark(pl, st, kStageWindow, ev));
         k_period_finalize<<<(cnt + 127) / 128, 128, 0, st>>>(dp, dc, dk, dq, p0, cnt);
