@@ -47,6 +47,9 @@ def _args():
                     help="target CPU time of the oracle sample (cpu_baseline / reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--periods-per-chunk", type=int, default=0,
+                    help="periods per kernel wave (0 = library default); small values shrink "
+                         "the device footprint for profiler captures")
     return ap.parse_args()
 
 
@@ -240,7 +243,8 @@ def run_gtls(args):
     cfg = lc.search
     plan = pkg.Plan(pkg.PlanConfig(baseline_days=lc.baseline_days, n_points=lc.n,
                                    period_min_days=cfg["period_min_days"],
-                                   period_max_days=cfg["period_max_days"]))
+                                   period_max_days=cfg["period_max_days"],
+                                   periods_per_chunk=args.periods_per_chunk))
     info = {"n_periods": plan.n_periods, "wpe": float(plan.info.wpe),
             "n_windows": int(plan.info.n_windows)}
     t = torch.as_tensor(lc.t, dtype=torch.float64, device=dev)

@@ -70,7 +70,7 @@ typedef struct {
     double dt0;                 /* T0 step as a fraction of D (default 0.05) */
     double u1, u2;              /* quadratic limb darkening (default 0.4, 0.25) */
     int32_t median_window;      /* odd SDE median window; 0 => 2 floor(N_P/200) + 1 */
-    int32_t reserved0;
+    int32_t periods_per_chunk;  /* periods folded per kernel wave; 0 => fit 2 GiB of scratch */
     const double* periods_days; /* optional explicit period grid (host, copied); NULL => Ofir */
     int64_t n_periods;          /* length of periods_days */
 } gtls_plan_params;

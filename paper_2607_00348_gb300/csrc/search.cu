@@ -850,6 +850,7 @@ gtls_status create_device(gtls_plan* pl)
     const int64_t budget = int64_t(1) << 31;  // 2 GiB of chunk scratch
     int64_t chunk = std::max<int64_t>(1, budget / per_period);
     chunk = std::min<int64_t>(chunk, 1024);
+    if (h.prm.periods_per_chunk > 0) chunk = h.prm.periods_per_chunk;
     chunk = std::min<int64_t>(chunk, dp.np);
     dk.chunk = (int32_t)chunk;
     GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.fold_stride));

@@ -43,7 +43,7 @@ class PlanParams(ctypes.Structure):
                 ("k_max", ctypes.c_double), ("q_cap", ctypes.c_double),
                 ("dur_ratio", ctypes.c_double), ("dt0", ctypes.c_double),
                 ("u1", ctypes.c_double), ("u2", ctypes.c_double),
-                ("median_window", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("median_window", ctypes.c_int32), ("periods_per_chunk", ctypes.c_int32),
                 ("periods_days", c_double_p), ("n_periods", ctypes.c_int64)]
 
 
@@ -176,6 +176,7 @@ class PlanConfig:
     u1: float = 0.4
     u2: float = 0.25
     median_window: int = 0
+    periods_per_chunk: int = 0
     periods_days: np.ndarray | None = None
 
 
@@ -188,7 +189,7 @@ class Plan:
         lib.gtls_plan_params_default(ctypes.byref(prm))
         for f in ("baseline_days", "n_points", "m_star", "r_star", "oversampling",
                   "period_min_days", "period_max_days", "k_min", "k_max", "q_cap",
-                  "dur_ratio", "dt0", "u1", "u2", "median_window"):
+                  "dur_ratio", "dt0", "u1", "u2", "median_window", "periods_per_chunk"):
             v = getattr(cfg, f)
             setattr(prm, f, v if v is not None else 0)
         self._periods_in = None
