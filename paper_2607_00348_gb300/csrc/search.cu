@@ -461,35 +461,57 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             tile_smem[i] = i < valid ? src[i] : 0.0f;
 
         // durations of the period, longest first, with their task ranges
-        if (threadIdx.x == 0) {
+        // (warp 0: one lane per candidate duration, ballot-compacted)
+        if (warp == 0) {
             const int lo = dp.jlo[p], hi = dp.jhi[p];
-            int k = 0, total = 0;
-            for (int j = hi; j >= lo; --j) {
-                if (j > lo && dp.dpts[j] == dp.dpts[j - 1]) continue;
-                if (!in_range(dc.check, 19, k, kMaxDur)) break;
-                DurTask t;
-                t.j = j;
-                t.d = dp.dpts[j];
-                t.st = dp.stride[j];
-                t.m_total = (int)((n + t.st - 1) / t.st);
-                t.m_a = (x0 + t.st - 1) / t.st;
-                t.m_b = min(t.m_total, (x0 + tc.len + t.st - 1) / t.st);
-                const int nwin = max(0, t.m_b - t.m_a);
-                pick_config(t.st, max(1, nwin), t.variant, t.nc);
-                t.w = variant_w(t.variant);
-                t.per_task = 32 * t.w / t.nc;
-                t.tasks = (nwin + t.per_task - 1) / t.per_task;
-                const int jrows = (t.d + t.st - 1) / t.st;
-                const int m_max_start = (x0 + tc.buf) / t.st - t.w - jrows;
-                t.hi_start = min(t.m_total - t.w, m_max_start);
-                if (t.tasks > 0) in_range(dc.check, 20, (int64_t)t.m_a, (int64_t)m_max_start + 1);
-                t.first = total;
-                total += t.tasks;
-                dur[k++] = t;
+            int kcount = 0;
+            for (int base = 0; base <= hi - lo; base += 32) {
+                const int j = hi - base - lane;
+                const bool kept = j >= lo && (j == lo || dp.dpts[j] != dp.dpts[j - 1]);
+                const unsigned int mask = __ballot_sync(0xffffffffu, kept);
+                const int k = kcount + __popc(mask & ((1u << lane) - 1u));
+                if (kept && in_range(dc.check, 19, k, kMaxDur)) {
+                    DurTask t;
+                    t.j = j;
+                    t.d = dp.dpts[j];
+                    t.st = dp.stride[j];
+                    t.m_total = (int)((n + t.st - 1) / t.st);
+                    t.m_a = (x0 + t.st - 1) / t.st;
+                    t.m_b = min(t.m_total, (x0 + tc.len + t.st - 1) / t.st);
+                    const int nwin = max(0, t.m_b - t.m_a);
+                    pick_config(t.st, max(1, nwin), t.variant, t.nc);
+                    t.w = variant_w(t.variant);
+                    t.per_task = 32 * t.w / t.nc;
+                    t.tasks = (nwin + t.per_task - 1) / t.per_task;
+                    const int jrows = (t.d + t.st - 1) / t.st;
+                    const int m_max_start = (x0 + tc.buf) / t.st - t.w - jrows;
+                    t.hi_start = min(t.m_total - t.w, m_max_start);
+                    if (t.tasks > 0) in_range(dc.check, 20, (int64_t)t.m_a, (int64_t)m_max_start + 1);
+                    t.first = 0;
+                    dur[k] = t;
+                }
+                kcount += __popc(mask);
             }
-            s_ndur = k;
-            s_total = total;
-            s_task = 0;
+            kcount = min(kcount, kMaxDur);
+            __syncwarp();
+            int run = 0;
+            for (int base = 0; base < kcount; base += 32) {
+                const int k = base + lane;
+                const int tk = k < kcount ? dur[k].tasks : 0;
+                int incl = tk;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (k < kcount) dur[k].first = run + incl - tk;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) {
+                s_ndur = kcount;
+                s_total = run;
+                s_task = 0;
+            }
         }
         __syncthreads();
 
@@ -823,7 +845,15 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.dpts), h.dpts));
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.stride), h.stride));
     GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl_off), h.tmpl_off));
-    GTLS_TRY(upload(pl, const_cast<float**>(&dp.tmpl), h.tmpl));
+    {
+        // zeros past the last template: the window kernel prefetches one
+        // template row ahead without a bounds test
+        std::vector<float> tmpl_pad(h.tmpl);
+        int st_max = 1;
+        for (int v : h.stride) st_max = std::max(st_max, v);
+        tmpl_pad.resize(h.tmpl.size() + (size_t)st_max + 64, 0.0f);
+        GTLS_TRY(upload(pl, const_cast<float**>(&dp.tmpl), tmpl_pad));
+    }
     GTLS_TRY(upload(pl, const_cast<float**>(&dp.inv_sum_t), inv_sum_t));
     GTLS_TRY(upload(pl, const_cast<float**>(&dp.sum_t2), sum_t2f));
     GTLS_TRY(upload(pl, const_cast<double**>(&dp.sum_t), h.sum_t));

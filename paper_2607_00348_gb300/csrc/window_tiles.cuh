@@ -140,9 +140,11 @@ __device__ void warp_task_pair(const WinCtx& c, int lane, unsigned long long& be
     for (int w = 0; w < H; ++w) acc[w] = make_float2(0.0f, 0.0f);
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
+        float tv = __ldg(c.tg + cl);               // template row 0 of the first round
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            const float* tp = c.tg + rho;
+            const float* tp = c.tg + rho + st;       // next template row to fetch
+            const float t_round = __ldg(c.tg + rho + c.nc);   // row 0 of the next round
             const int jn = (c.d - rho + st - 1) / st;
             float2 p[H];
 #pragma unroll
@@ -155,9 +157,9 @@ __device__ void warp_task_pair(const WinCtx& c, int lane, unsigned long long& be
             for (; jj + H <= jn; jj += H) {
 #pragma unroll
                 for (int u = 0; u < H; ++u) {
-                    const float tv = __ldg(tp);
-                    tp += st;
                     const float2 t2 = make_float2(tv, tv);
+                    tv = __ldg(tp);                  // one row ahead (table is zero padded)
+                    tp += st;
 #pragma unroll
                     for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
                     p[u].x = p[u].y;
@@ -168,9 +170,9 @@ __device__ void warp_task_pair(const WinCtx& c, int lane, unsigned long long& be
 #pragma unroll
             for (int u = 0; u < H; ++u) {
                 if (jj + u < jn) {
-                    const float tv = __ldg(tp);
-                    tp += st;
                     const float2 t2 = make_float2(tv, tv);
+                    tv = __ldg(tp);
+                    tp += st;
 #pragma unroll
                     for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
                     p[u].x = p[u].y;
@@ -178,6 +180,7 @@ __device__ void warp_task_pair(const WinCtx& c, int lane, unsigned long long& be
                     an += st;
                 }
             }
+            tv = t_round;
         }
     }
     float tot[W];
@@ -202,9 +205,11 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
     for (int w = 0; w < W; ++w) acc[w] = 0.0f;
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
+        float tv = __ldg(c.tg + cl);
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            const float* tp = c.tg + rho;
+            const float* tp = c.tg + rho + st;
+            const float t_round = __ldg(c.tg + rho + c.nc);
             const int jn = (c.d - rho + st - 1) / st;
             float p[W];
 #pragma unroll
@@ -214,10 +219,11 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
             for (; jj + W <= jn; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
-                    const float tv = __ldg(tp);
+                    const float tcur = tv;
+                    tv = __ldg(tp);
                     tp += st;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tv, acc[w]);
+                    for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
                     p[u] = *an;
                     an += st;
                 }
@@ -225,14 +231,16 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
 #pragma unroll
             for (int u = 0; u < W; ++u) {
                 if (jj + u < jn) {
-                    const float tv = __ldg(tp);
+                    const float tcur = tv;
+                    tv = __ldg(tp);
                     tp += st;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tv, acc[w]);
+                    for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
                     p[u] = *an;
                     an += st;
                 }
             }
+            tv = t_round;
         }
     }
     reduce_finish<W>(c, acc, mb, active, lane, best);
