@@ -38,6 +38,10 @@ struct DevPlan {
     const double* sum_t;      // FP64 sum_k s_k
     const double* q;
     int64_t tmpl_total;       // floats in tmpl
+    const int32_t* cfg_variant; // window-kernel variant per duration (see window_tiles.cuh)
+    const int32_t* cfg_nc;      // phase-column lanes per window block per duration
+    const int64_t* tmpl2_off;   // offset of duration j in tmpl2 (float2 units)
+    const float2* tmpl2;        // template pairs (s_k, s_{k+nc}) of column-pair durations
 };
 
 // Per-light-curve derived arrays (n long unless noted).
@@ -102,6 +106,8 @@ struct gtls_plan {
     int tile_buf = 0, tile_len = 0, tile_count = 0;
     int n_sm = 0;
     unsigned int* tile_counter = nullptr;
+    std::vector<float> tmpl_pad;        // host copy of the zero-padded template table
+    std::vector<int64_t> tmpl_pad_off;
     // stage profiling: events recorded on the search stream when enabled
     bool profiling = false;
     std::vector<cudaEvent_t> events;

@@ -479,12 +479,15 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
                     t.m_a = (x0 + t.st - 1) / t.st;
                     t.m_b = min(t.m_total, (x0 + tc.len + t.st - 1) / t.st);
                     const int nwin = max(0, t.m_b - t.m_a);
-                    pick_config(t.st, max(1, nwin), t.variant, t.nc);
+                    t.variant = dp.cfg_variant[j];
+                    t.nc = dp.cfg_nc[j];
                     t.w = variant_w(t.variant);
                     t.per_task = 32 * t.w / t.nc;
                     t.tasks = (nwin + t.per_task - 1) / t.per_task;
                     const int jrows = (t.d + t.st - 1) / t.st;
-                    const int m_max_start = (x0 + tc.buf) / t.st - t.w - jrows;
+                    t.jrows = jrows;
+                    // rows up to m + w + jrows - 1 and columns up to st + 31 must stay in the buffer
+                    const int m_max_start = (x0 + tc.buf - 32) / t.st - t.w - jrows;
                     t.hi_start = min(t.m_total - t.w, m_max_start);
                     if (t.tasks > 0) in_range(dc.check, 20, (int64_t)t.m_a, (int64_t)m_max_start + 1);
                     t.first = 0;
@@ -532,6 +535,8 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             c.st = t.st;
             c.nc = t.nc;
             c.lg_nc = __ffs(t.nc) - 1;
+            c.jrows = t.jrows;
+            c.tg2 = dp.tmpl2 + dp.tmpl2_off[t.j];
             c.m_first = t.m_a + (task - t.first) * t.per_task;
             c.m_a = t.m_a;
             c.m_b = t.m_b;
@@ -544,10 +549,15 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             c.j = t.j;
             c.pf = dk.pf + (int64_t)slot * dk.pad_stride;
             switch (t.variant) {
-            case kPair16: warp_task_pair<16>(c, lane, best); break;
-            case kPair14: warp_task_pair<14>(c, lane, best); break;
-            case kPair12: warp_task_pair<12>(c, lane, best); break;
-            case kPair8: warp_task_pair<8>(c, lane, best); break;
+            case kWin16: warp_task_winpair<16>(c, lane, best); break;
+            case kWin14: warp_task_winpair<14>(c, lane, best); break;
+            case kWin12: warp_task_winpair<12>(c, lane, best); break;
+            case kWin8: warp_task_winpair<8>(c, lane, best); break;
+            case kCol16: warp_task_colpair<16>(c, lane, best); break;
+            case kCol15: warp_task_colpair<15>(c, lane, best); break;
+            case kCol14: warp_task_colpair<14>(c, lane, best); break;
+            case kCol12: warp_task_colpair<12>(c, lane, best); break;
+            case kCol8: warp_task_colpair<8>(c, lane, best); break;
             default: warp_task_scalar<15>(c, lane, best); break;
             }
         }
@@ -812,6 +822,75 @@ gtls_status upload(gtls_plan* pl, T** ptr, const std::vector<T>& v)
         if (s_ != GTLS_OK) return s_;   \
     } while (0)
 
+// Window-kernel variant and phase lanes for a T0 step st with about `nwin`
+// windows per tile: the candidates keep W st = nc * odd (mod 32) (bank
+// conflict free); the score is the useful fraction of lane slots times an
+// issue-rate factor of the variant.
+void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
+{
+    int v = 0;
+    while (v < 5 && ((st >> v) & 1) == 0) ++v;
+    double best = -1.0;
+    variant = tiles::kWin16;
+    nc_out = 32;
+    auto consider = [&](int var, int nc, double ipc) {
+        if (nc > 32 || nc < 1) return;
+        const int w = tiles::variant_w(var);
+        const int cols = tiles::variant_colpair(var) ? 2 * nc : nc;
+        const int rounds = (st + cols - 1) / cols;
+        const double util = (double)st / (double)(cols * rounds);
+        const int per = 32 * w / nc;
+        const int tasks = (nwin + per - 1) / per;
+        const double fill = (double)nwin / (double)(tasks * per);
+        const double eff = util * fill * ipc;
+        if (eff > best + 1e-9) {
+            best = eff;
+            variant = var;
+            nc_out = nc;
+        }
+    };
+    // issue-rate factor: min(1, 0.85 x FMA-pipe cycles / issue slots per row);
+    // a row costs the variant's FFMA(2)s plus ~7 (winpair), ~6 (colpair) or
+    // ~5 (scalar) other instructions
+    auto ipc = [](int var) {
+        const int w = tiles::variant_w(var);
+        double pipe, slots;
+        if (var == tiles::kScalar15) {
+            pipe = w;
+            slots = w + 5;
+        } else if (tiles::variant_colpair(var)) {
+            pipe = 2.0 * w;
+            slots = w + 6;
+        } else {
+            pipe = w;
+            slots = w / 2 + 7;
+        }
+        return std::min(1.0, 0.85 * pipe / slots);
+    };
+    consider(tiles::kWin16, 32, ipc(tiles::kWin16));
+    consider(tiles::kCol16, 32, ipc(tiles::kCol16));
+    if (v <= 4) {
+        consider(tiles::kScalar15, 1 << v, ipc(tiles::kScalar15));
+        consider(tiles::kCol15, 1 << v, ipc(tiles::kCol15));
+    }
+    if (v + 1 <= 5) {
+        consider(tiles::kWin14, 1 << (v + 1), ipc(tiles::kWin14));
+        consider(tiles::kCol14, 1 << (v + 1), ipc(tiles::kCol14));
+    }
+    if (v + 2 <= 5) {
+        consider(tiles::kWin12, 1 << (v + 2), ipc(tiles::kWin12));
+        consider(tiles::kCol12, 1 << (v + 2), ipc(tiles::kCol12));
+    }
+    if (v + 3 <= 5) {
+        consider(tiles::kWin8, 1 << (v + 3), ipc(tiles::kWin8));
+        consider(tiles::kCol8, 1 << (v + 3), ipc(tiles::kCol8));
+    }
+    if (v + 4 <= 5) {
+        consider(tiles::kWin16, 1 << (v + 4), ipc(tiles::kWin16));
+        consider(tiles::kCol16, 1 << (v + 4), ipc(tiles::kCol16));
+    }
+}
+
 int fold_smem_bytes(int bucket_log2)
 {
     return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long);
@@ -844,15 +923,25 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.dmax_p), h.dmax_p));
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.dpts), h.dpts));
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.stride), h.stride));
-    GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl_off), h.tmpl_off));
     {
-        // zeros past the last template: the window kernel prefetches one
-        // template row ahead without a bounds test
-        std::vector<float> tmpl_pad(h.tmpl);
-        int st_max = 1;
-        for (int v : h.stride) st_max = std::max(st_max, v);
-        tmpl_pad.resize(h.tmpl.size() + (size_t)st_max + 64, 0.0f);
+        // every template is followed by 2 st + 64 zeros: the window kernels
+        // run ceil(D / st) rows for every phase column and prefetch one row
+        // ahead without bounds tests
+        std::vector<int64_t> off(dp.nd);
+        int64_t pos = 0;
+        for (int j = 0; j < dp.nd; ++j) {
+            off[j] = pos;
+            pos += h.dpts[j] + 2 * (int64_t)h.stride[j] + 64;
+        }
+        std::vector<float> tmpl_pad((size_t)pos, 0.0f);
+        for (int j = 0; j < dp.nd; ++j)
+            std::copy(h.tmpl.begin() + h.tmpl_off[j], h.tmpl.begin() + h.tmpl_off[j] + h.dpts[j],
+                      tmpl_pad.begin() + off[j]);
         GTLS_TRY(upload(pl, const_cast<float**>(&dp.tmpl), tmpl_pad));
+        GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl_off), off));
+        dp.tmpl_total = pos;
+        pl->tmpl_pad = std::move(tmpl_pad);
+        pl->tmpl_pad_off = std::move(off);
     }
     GTLS_TRY(upload(pl, const_cast<float**>(&dp.inv_sum_t), inv_sum_t));
     GTLS_TRY(upload(pl, const_cast<float**>(&dp.sum_t2), sum_t2f));
@@ -871,7 +960,6 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(dev_alloc(pl, &dc.flags, 1));
     GTLS_TRY(dev_alloc(pl, &dc.part, 1024));
     GTLS_TRY(dev_alloc(pl, &dc.check, 4));
-    dp.tmpl_total = (int64_t)h.tmpl.size();
 
     DevChunk& dk = pl->dk;
     dk.fold_stride = (n + 31) & ~int64_t(31);
@@ -920,17 +1008,47 @@ gtls_status create_device(gtls_plan* pl)
         for (int j = 0; j < dp.nd; ++j) {
             st_max = std::max(st_max, h.stride[j]);
             const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
-            if ((int64_t)(16 + jrows + 2) * h.stride[j] > buf) fits = false;
+            if ((int64_t)(16 + jrows + 2) * h.stride[j] + 32 > buf) fits = false;
         }
-        const int64_t len = ((int64_t)buf - h.dmax - 3 * (int64_t)st_max - 64) & ~int64_t(63);
+        const int64_t len = ((int64_t)buf - h.dmax - 3 * (int64_t)st_max - 96) & ~int64_t(63);
         pl->tile_ok = fits && len >= 64;
+        std::vector<int32_t> var(dp.nd, tiles::kWin16), ncs(dp.nd, 32);
+        std::vector<int64_t> off2(dp.nd, 0);
+        std::vector<float2> t2;
         if (pl->tile_ok) {
             pl->tile_buf = buf;
             pl->tile_len = (int)len;
             pl->tile_count = (int)((n + len - 1) / len);
             GTLS_CUDA(cudaFuncSetAttribute(k_window_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            buf * (int)sizeof(float)));
+            int64_t pos2 = 0;
+            for (int j = 0; j < dp.nd; ++j) {
+                const int st = h.stride[j];
+                const int64_t m_total = (n + st - 1) / st;
+                const int nwin = (int)std::min<int64_t>(m_total, (len + st - 1) / st);
+                pick_config_host(st, nwin, var[j], ncs[j]);
+                off2[j] = pos2;
+                if (tiles::variant_colpair(var[j])) pos2 += h.dpts[j] + 2 * (int64_t)st + 64;
+            }
+            t2.assign((size_t)std::max<int64_t>(pos2, 1), make_float2(0.0f, 0.0f));
+            for (int j = 0; j < dp.nd; ++j) {
+                if (!tiles::variant_colpair(var[j])) continue;
+                const int st = h.stride[j], d = h.dpts[j], nc = ncs[j];
+                const float* tj = pl->tmpl_pad.data() + pl->tmpl_pad_off[j];
+                const int64_t len2 = d + 2 * (int64_t)st + 64;
+                for (int64_t k = 0; k < len2; ++k) {
+                    const int rho = (int)(k % st);
+                    const float x = k < d ? tj[k] : 0.0f;
+                    const float y = (rho + nc < st && k + nc < d) ? tj[k + nc] : 0.0f;
+                    t2[(size_t)(off2[j] + k)] = make_float2(x, y);
+                }
+            }
         }
+        GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_variant), var));
+        GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_nc), ncs));
+        GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl2_off), off2));
+        if (t2.empty()) t2.assign(1, make_float2(0.0f, 0.0f));
+        GTLS_TRY(upload(pl, const_cast<float2**>(&dp.tmpl2), t2));
         GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
     }
     GTLS_CUDA(cudaFuncSetAttribute(k_fold_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,

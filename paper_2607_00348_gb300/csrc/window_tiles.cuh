@@ -13,17 +13,24 @@
 //           folded curve [x0, x0 + BUF) in shared memory once and evaluates
 //           every duration of the period on it.
 //   task  = one warp, one duration, 32 W / nc consecutive windows.
-//           Lane (b, c): block b of W consecutive windows, phase class c of
-//           the T0 stride (rho = c, c + nc, ...; rows of st points).  For a
-//           fixed rho, window w needs rows w .. w+J-1 of column rho, so a
-//           register window slides down the rows: one shared load feeds W
-//           FMAs.  Pairs of windows (w, w + W/2) share one FFMA2.
-//           nc and W are chosen so that the lanes of a warp hit 32 distinct
-//           shared-memory banks: W st = nc * odd (mod 32).
+//           The folded curve is read as rows of st points: window m covers
+//           rows m .. m+J-1 (J = ceil(D / st)) of every phase column rho.
+//           Lane (b, c) owns block b of W consecutive windows and the
+//           columns rho = c, c + nc, ...; for a fixed column a register
+//           ring of W rows slides down the rows, so one shared load feeds W
+//           FMAs.  nc and W satisfy W st = nc * odd (mod 32): the 32 lanes
+//           then read 32 distinct shared-memory banks.
+//   Variants (chosen per duration when the plan is made):
+//     colpair<W>  one FFMA2 per window covers the two columns rho, rho + nc
+//                 (template pairs come from a per-duration pair table whose
+//                 second value is zero where rho + nc >= st);
+//     winpair<W>  one FFMA2 covers windows w and w + W/2 of one column;
+//     scalar<15>  plain FFMA (strides that are small powers of two).
+//   Templates are followed by zeros, so every lane runs the same J steps.
 //   The nc lanes of a block add their partial sums with a butterfly; each
 //   lane then finishes W / nc windows and keeps a packed running minimum
-//   (delta-chi2 key, duration index, window index), merged per period
-//   with one 64-bit atomicMin.
+//   (delta-chi2 key, duration index, window index), merged per period with
+//   one 64-bit atomicMin.
 #pragma once
 
 namespace gtls {
@@ -33,54 +40,50 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxDur = 64;
 
-enum Variant : int { kScalar15 = 0, kPair16 = 1, kPair14 = 2, kPair12 = 3, kPair8 = 4 };
-
-struct DurTask {
-    int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total;
+// Variant codes (also used by the host plan).
+enum Variant : int {
+    kScalar15 = 0,
+    kWin16 = 1,
+    kWin14 = 2,
+    kWin12 = 3,
+    kWin8 = 4,
+    kCol16 = 5,
+    kCol15 = 6,
+    kCol14 = 7,
+    kCol12 = 8,
+    kCol8 = 9,
 };
 
-__device__ __forceinline__ int variant_w(int v)
+__host__ __device__ inline int variant_w(int v)
 {
-    return v == kScalar15 ? 15 : v == kPair16 ? 16 : v == kPair14 ? 14 : v == kPair12 ? 12 : 8;
+    switch (v) {
+    case kScalar15: return 15;
+    case kWin16: return 16;
+    case kWin14: return 14;
+    case kWin12: return 12;
+    case kWin8: return 8;
+    case kCol16: return 16;
+    case kCol15: return 15;
+    case kCol14: return 14;
+    case kCol12: return 12;
+    default: return 8;
+    }
 }
 
-// Pick (variant, nc) for a duration with T0 step st and `nwin` windows in the tile.
-__device__ void pick_config(int st, int nwin, int& variant, int& nc)
-{
-    const int v = min(5, __ffs(st) - 1);
-    float best = -1.0f;
-    variant = kPair16;
-    nc = 32;
-    auto consider = [&](int var, int c_nc, float ipc) {
-        if (c_nc > 32) return;
-        const int w = variant_w(var);
-        const int rounds = (st + c_nc - 1) / c_nc;
-        const float util = (float)st / (float)(c_nc * rounds);
-        const int per = 32 * w / c_nc;
-        const int tasks = (nwin + per - 1) / per;
-        const float fill = (float)nwin / (float)(tasks * per);
-        const float eff = util * fill * ipc;
-        if (eff > best) {
-            best = eff;
-            variant = var;
-            nc = c_nc;
-        }
-    };
-    consider(kPair16, 32, 1.0f);
-    if (v <= 4) consider(kScalar15, 1 << v, 0.85f);
-    if (v + 1 <= 5) consider(kPair14, 1 << (v + 1), 1.0f);
-    if (v + 2 <= 5) consider(kPair12, 1 << (v + 2), 1.0f);
-    if (v + 3 <= 5) consider(kPair8, 1 << (v + 3), 0.9f);
-    if (v + 4 <= 5) consider(kPair16, 1 << (v + 4), 1.0f);
-}
+__host__ __device__ inline bool variant_colpair(int v) { return v >= kCol16; }
+
+struct DurTask {
+    int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total, jrows;
+};
 
 struct WinCtx {
     const float* tile;        // shared: folded r at x0 .. x0 + BUF
     int x0;
-    int d, st, nc, lg_nc;
+    int d, st, nc, lg_nc, jrows;
     int m_first;              // first window of this warp task
     int m_a, m_b, hi_start, m_total;
-    const float* tg;          // template of the duration (global)
+    const float* tg;          // template of the duration (global, zero padded)
+    const float2* tg2;        // template pairs (colpair variants)
     float inv_sum_t, sum_t2, w_uni;
     int j;
     const long long* pf;      // prefix sums of the period (global)
@@ -126,50 +129,97 @@ __device__ __forceinline__ int block_start(const WinCtx& c, int b, int w, bool& 
     return max(c.m_a, min(m0, c.hi_start));
 }
 
+// Column pairs: acc[w] = (column rho, column rho + nc) partial sums of window w.
 template <int W>
-__device__ void warp_task_pair(const WinCtx& c, int lane, unsigned long long& best)
+__device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long& best)
+{
+    const int b = lane >> c.lg_nc;
+    const int cl = lane & (c.nc - 1);
+    bool active;
+    const int mb = block_start(c, b, W, active);
+    const int st = c.st, nc = c.nc, jrows = c.jrows;
+    float2 acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = make_float2(0.0f, 0.0f);
+    if (active) {
+        const float* abase = c.tile + (mb * st - c.x0);
+        for (int rho = cl; rho < st; rho += 2 * nc) {
+            const float* a = abase + rho;
+            const float2* tp = c.tg2 + rho;
+            float2 p[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                p[w].x = a[w * st];
+                p[w].y = a[w * st + nc];
+            }
+            float2 tv = __ldg(tp);
+            tp += st;
+            const float* an = a + W * st;
+            int jj = 0;
+            for (; jj + W <= jrows; jj += W) {
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const float2 tcur = tv;
+                    tv = __ldg(tp);          // next row (the pair table is zero padded)
+                    tp += st;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+                    p[u].x = an[0];
+                    p[u].y = an[nc];
+                    an += st;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (jj + u >= jrows) break;
+                const float2 tcur = tv;
+                tv = __ldg(tp);
+                tp += st;
+#pragma unroll
+                for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+                p[u].x = an[0];
+                p[u].y = an[nc];
+                an += st;
+            }
+        }
+    }
+    float tot[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) tot[w] = acc[w].x + acc[w].y;
+    reduce_finish<W>(c, tot, mb, active, lane, best);
+}
+
+// Window pairs: acc[w] = (window w, window w + W/2) partial sums of one column.
+template <int W>
+__device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long& best)
 {
     constexpr int H = W / 2;
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
     const int mb = block_start(c, b, W, active);
-    const int st = c.st;
+    const int st = c.st, jrows = c.jrows;
     float2 acc[H];
 #pragma unroll
     for (int w = 0; w < H; ++w) acc[w] = make_float2(0.0f, 0.0f);
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
-        float tv = __ldg(c.tg + cl);               // template row 0 of the first round
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            const float* tp = c.tg + rho + st;       // next template row to fetch
-            const float t_round = __ldg(c.tg + rho + c.nc);   // row 0 of the next round
-            const int jn = (c.d - rho + st - 1) / st;
+            const float* tp = c.tg + rho;
             float2 p[H];
 #pragma unroll
             for (int w = 0; w < H; ++w) {
                 p[w].x = a[w * st];
                 p[w].y = a[(w + H) * st];
             }
+            float tv = __ldg(tp);
+            tp += st;
             const float* an = a + W * st;
             int jj = 0;
-            for (; jj + H <= jn; jj += H) {
+            for (; jj + H <= jrows; jj += H) {
 #pragma unroll
                 for (int u = 0; u < H; ++u) {
-                    const float2 t2 = make_float2(tv, tv);
-                    tv = __ldg(tp);                  // one row ahead (table is zero padded)
-                    tp += st;
-#pragma unroll
-                    for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
-                    p[u].x = p[u].y;
-                    p[u].y = *an;
-                    an += st;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < H; ++u) {
-                if (jj + u < jn) {
                     const float2 t2 = make_float2(tv, tv);
                     tv = __ldg(tp);
                     tp += st;
@@ -180,7 +230,18 @@ __device__ void warp_task_pair(const WinCtx& c, int lane, unsigned long long& be
                     an += st;
                 }
             }
-            tv = t_round;
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                if (jj + u >= jrows) break;
+                const float2 t2 = make_float2(tv, tv);
+                tv = __ldg(tp);
+                tp += st;
+#pragma unroll
+                for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
+                p[u].x = p[u].y;
+                p[u].y = *an;
+                an += st;
+            }
         }
     }
     float tot[W];
@@ -199,24 +260,23 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
     const int cl = lane & (c.nc - 1);
     bool active;
     const int mb = block_start(c, b, W, active);
-    const int st = c.st;
+    const int st = c.st, jrows = c.jrows;
     float acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = 0.0f;
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
-        float tv = __ldg(c.tg + cl);
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            const float* tp = c.tg + rho + st;
-            const float t_round = __ldg(c.tg + rho + c.nc);
-            const int jn = (c.d - rho + st - 1) / st;
+            const float* tp = c.tg + rho;
             float p[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) p[w] = a[w * st];
+            float tv = __ldg(tp);
+            tp += st;
             const float* an = a + W * st;
             int jj = 0;
-            for (; jj + W <= jn; jj += W) {
+            for (; jj + W <= jrows; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     const float tcur = tv;
@@ -230,17 +290,15 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
             }
 #pragma unroll
             for (int u = 0; u < W; ++u) {
-                if (jj + u < jn) {
-                    const float tcur = tv;
-                    tv = __ldg(tp);
-                    tp += st;
+                if (jj + u >= jrows) break;
+                const float tcur = tv;
+                tv = __ldg(tp);
+                tp += st;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
-                    p[u] = *an;
-                    an += st;
-                }
+                for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
+                p[u] = *an;
+                an += st;
             }
-            tv = t_round;
         }
     }
     reduce_finish<W>(c, acc, mb, active, lane, best);
