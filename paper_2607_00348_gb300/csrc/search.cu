@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -543,22 +544,21 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             c.hi_start = t.hi_start;
             c.m_total = t.m_total;
             c.tg = dp.tmpl + dp.tmpl_off[t.j];
-            c.inv_sum_t = dp.inv_sum_t[t.j];
+            c.inv_sum_t = dp.inv_sum_t[t.j] * (1.0f / 1099511627776.0f);  // 2^-40 fixed point
             c.sum_t2 = dp.sum_t2[t.j];
             c.w_uni = w_uni;
             c.j = t.j;
             c.pf = dk.pf + (int64_t)slot * dk.pad_stride;
             switch (t.variant) {
-            case kWin16: warp_task_winpair<16>(c, lane, best); break;
-            case kWin14: warp_task_winpair<14>(c, lane, best); break;
-            case kWin12: warp_task_winpair<12>(c, lane, best); break;
-            case kWin8: warp_task_winpair<8>(c, lane, best); break;
-            case kCol16: warp_task_colpair<16>(c, lane, best); break;
-            case kCol15: warp_task_colpair<15>(c, lane, best); break;
-            case kCol14: warp_task_colpair<14>(c, lane, best); break;
-            case kCol12: warp_task_colpair<12>(c, lane, best); break;
-            case kCol8: warp_task_colpair<8>(c, lane, best); break;
-            default: warp_task_scalar<15>(c, lane, best); break;
+            case kWin16: warp_task_winpair<16, 4>(c, lane, best); break;
+            case kWin14: warp_task_winpair<14, 7>(c, lane, best); break;
+            case kWin12: warp_task_winpair<12, 6>(c, lane, best); break;
+            case kWin8: warp_task_winpair<8, 4>(c, lane, best); break;
+            case kCol16: warp_task_colpair<16, 4>(c, lane, best); break;
+            case kCol15: warp_task_colpair<15, 5>(c, lane, best); break;
+            case kCol12: warp_task_colpair<12, 4>(c, lane, best); break;
+            case kCol8: warp_task_colpair<8, 4>(c, lane, best); break;
+            default: warp_task_scalar<15, 5>(c, lane, best); break;
             }
         }
 #pragma unroll
@@ -875,7 +875,6 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
     }
     if (v + 1 <= 5) {
         consider(tiles::kWin14, 1 << (v + 1), ipc(tiles::kWin14));
-        consider(tiles::kCol14, 1 << (v + 1), ipc(tiles::kCol14));
     }
     if (v + 2 <= 5) {
         consider(tiles::kWin12, 1 << (v + 2), ipc(tiles::kWin12));
@@ -924,14 +923,14 @@ gtls_status create_device(gtls_plan* pl)
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.dpts), h.dpts));
     GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.stride), h.stride));
     {
-        // every template is followed by 2 st + 64 zeros: the window kernels
-        // run ceil(D / st) rows for every phase column and prefetch one row
-        // ahead without bounds tests
+        // every template is followed by (kMaxRing + 2) st + 64 zeros: the
+        // window kernels run ceil(D / st) rows for every phase column and
+        // fetch template rows up to kMaxRing rows ahead without bounds tests
         std::vector<int64_t> off(dp.nd);
         int64_t pos = 0;
         for (int j = 0; j < dp.nd; ++j) {
             off[j] = pos;
-            pos += h.dpts[j] + 2 * (int64_t)h.stride[j] + 64;
+            pos += h.dpts[j] + (tiles::kMaxRing + 2) * (int64_t)h.stride[j] + 64;
         }
         std::vector<float> tmpl_pad((size_t)pos, 0.0f);
         for (int j = 0; j < dp.nd; ++j)
@@ -1002,7 +1001,24 @@ gtls_status create_device(gtls_plan* pl)
         int smem_optin = 0;
         GTLS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         const int static_bytes = 8192;  // duration table and reduction scratch, rounded up
-        const int buf = std::min(55296, (smem_optin - static_bytes) / 4) & ~63;
+        // floats of folded curve staged per tile; the rest of the SM's
+        // unified L1/shared memory caches the template tables
+        int want = 32768;
+        if (const char* e = std::getenv("GTLS_TILE_FLOATS")) want = std::max(4096, std::atoi(e));
+        int buf = std::min(want, (smem_optin - static_bytes) / 4) & ~63;
+        {
+            // the largest T0 step must fit one register block of rows
+            int need = 0;
+            for (int j = 0; j < dp.nd; ++j) {
+                const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
+                need = std::max(need, (16 + jrows + 2) * h.stride[j] + 32);
+            }
+            const int need_len = (int)std::min<int64_t>(h.n, 4096);
+            int st_mx = 1;
+            for (int v : h.stride) st_mx = std::max(st_mx, v);
+            need = std::max<int64_t>(need, need_len + h.dmax + 3 * (int64_t)st_mx + 96 + 63);
+            buf = std::max(buf, std::min((int)((need + 63) & ~63), (smem_optin - static_bytes) / 4 & ~63));
+        }
         int st_max = 1;
         bool fits = buf > 0;
         for (int j = 0; j < dp.nd; ++j) {
@@ -1028,14 +1044,14 @@ gtls_status create_device(gtls_plan* pl)
                 const int nwin = (int)std::min<int64_t>(m_total, (len + st - 1) / st);
                 pick_config_host(st, nwin, var[j], ncs[j]);
                 off2[j] = pos2;
-                if (tiles::variant_colpair(var[j])) pos2 += h.dpts[j] + 2 * (int64_t)st + 64;
+                if (tiles::variant_colpair(var[j])) pos2 += h.dpts[j] + (tiles::kMaxRing + 2) * (int64_t)st + 64;
             }
             t2.assign((size_t)std::max<int64_t>(pos2, 1), make_float2(0.0f, 0.0f));
             for (int j = 0; j < dp.nd; ++j) {
                 if (!tiles::variant_colpair(var[j])) continue;
                 const int st = h.stride[j], d = h.dpts[j], nc = ncs[j];
                 const float* tj = pl->tmpl_pad.data() + pl->tmpl_pad_off[j];
-                const int64_t len2 = d + 2 * (int64_t)st + 64;
+                const int64_t len2 = d + (tiles::kMaxRing + 2) * (int64_t)st + 64;
                 for (int64_t k = 0; k < len2; ++k) {
                     const int rho = (int)(k % st);
                     const float x = k < d ? tj[k] : 0.0f;

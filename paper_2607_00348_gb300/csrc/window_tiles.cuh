@@ -26,7 +26,8 @@
 //                 second value is zero where rho + nc >= st);
 //     winpair<W>  one FFMA2 covers windows w and w + W/2 of one column;
 //     scalar<15>  plain FFMA (strides that are small powers of two).
-//   Templates are followed by zeros, so every lane runs the same J steps.
+//   Templates are followed by zeros, so every lane runs the same J steps
+//   and template rows can be fetched several rows ahead (register ring).
 //   The nc lanes of a block add their partial sums with a butterfly; each
 //   lane then finishes W / nc windows and keeps a packed running minimum
 //   (delta-chi2 key, duration index, window index), merged per period with
@@ -39,6 +40,7 @@ namespace tiles {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxDur = 64;
+constexpr int kMaxRing = 7;   // template rows fetched ahead; tables carry (kMaxRing + 2) st + 64 zeros
 
 // Variant codes (also used by the host plan).
 enum Variant : int {
@@ -89,12 +91,21 @@ struct WinCtx {
     const long long* pf;      // prefix sums of the period (global)
 };
 
+// Exact 64-bit window sum of r (fixed point, 2^40) to float through two
+// 32-bit conversions (the FP64 pipe is narrow on this GPU); c.inv_sum_t
+// already carries the 2^-40 scale.
+__device__ __forceinline__ float fixed_to_float(long long v)
+{
+    const float hi = (float)(int)(v >> 32);
+    const float lo = (float)(unsigned int)(v & 0xffffffffll);
+    return fmaf(hi, 4294967296.0f, lo);
+}
+
 __device__ __forceinline__ unsigned long long finish_window(const WinCtx& c, long long m, float c1)
 {
     const long long s = m * c.st;
     const long long sfx = c.pf[s + c.d] - c.pf[s];
-    const float sum_r = (float)((double)sfx * (1.0 / 1099511627776.0));
-    const float depth = fmaxf(0.0f, sum_r * c.inv_sum_t);
+    const float depth = fmaxf(0.0f, fixed_to_float(sfx) * c.inv_sum_t);
     const float dchi = c.w_uni * depth * fmaf(depth, c.sum_t2, -2.0f * c1);
     unsigned int u = __float_as_uint(dchi);
     u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -130,9 +141,11 @@ __device__ __forceinline__ int block_start(const WinCtx& c, int b, int w, bool& 
 }
 
 // Column pairs: acc[w] = (column rho, column rho + nc) partial sums of window w.
-template <int W>
+// Template rows are fetched R rows ahead into a register ring (R divides W).
+template <int W, int R>
 __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long& best)
 {
+    static_assert(W % R == 0, "ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -146,21 +159,23 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
         for (int rho = cl; rho < st; rho += 2 * nc) {
             const float* a = abase + rho;
             const float2* tp = c.tg2 + rho;
+            float2 ring[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
+            tp += R * st;
             float2 p[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 p[w].x = a[w * st];
                 p[w].y = a[w * st + nc];
             }
-            float2 tv = __ldg(tp);
-            tp += st;
             const float* an = a + W * st;
             int jj = 0;
             for (; jj + W <= jrows; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
-                    const float2 tcur = tv;
-                    tv = __ldg(tp);          // next row (the pair table is zero padded)
+                    const float2 tcur = ring[u % R];
+                    ring[u % R] = __ldg(tp);     // row jj + u + R (zero padded past D)
                     tp += st;
 #pragma unroll
                     for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
@@ -172,8 +187,8 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
 #pragma unroll
             for (int u = 0; u < W; ++u) {
                 if (jj + u >= jrows) break;
-                const float2 tcur = tv;
-                tv = __ldg(tp);
+                const float2 tcur = ring[u % R];
+                ring[u % R] = __ldg(tp);
                 tp += st;
 #pragma unroll
                 for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
@@ -190,10 +205,12 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
 }
 
 // Window pairs: acc[w] = (window w, window w + W/2) partial sums of one column.
-template <int W>
+// Template rows come R rows ahead from a register ring (R divides W/2).
+template <int W, int R>
 __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long& best)
 {
     constexpr int H = W / 2;
+    static_assert(H % R == 0, "ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -207,22 +224,25 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
             const float* tp = c.tg + rho;
+            float ring[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
+            tp += R * st;
             float2 p[H];
 #pragma unroll
             for (int w = 0; w < H; ++w) {
                 p[w].x = a[w * st];
                 p[w].y = a[(w + H) * st];
             }
-            float tv = __ldg(tp);
-            tp += st;
             const float* an = a + W * st;
             int jj = 0;
             for (; jj + H <= jrows; jj += H) {
 #pragma unroll
                 for (int u = 0; u < H; ++u) {
-                    const float2 t2 = make_float2(tv, tv);
-                    tv = __ldg(tp);
+                    const float tv = ring[u % R];
+                    ring[u % R] = __ldg(tp);
                     tp += st;
+                    const float2 t2 = make_float2(tv, tv);
 #pragma unroll
                     for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
                     p[u].x = p[u].y;
@@ -233,9 +253,10 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
 #pragma unroll
             for (int u = 0; u < H; ++u) {
                 if (jj + u >= jrows) break;
-                const float2 t2 = make_float2(tv, tv);
-                tv = __ldg(tp);
+                const float tv = ring[u % R];
+                ring[u % R] = __ldg(tp);
                 tp += st;
+                const float2 t2 = make_float2(tv, tv);
 #pragma unroll
                 for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
                 p[u].x = p[u].y;
@@ -253,9 +274,10 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
     reduce_finish<W>(c, tot, mb, active, lane, best);
 }
 
-template <int W>
+template <int W, int R>
 __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& best)
 {
+    static_assert(W % R == 0, "ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -269,18 +291,20 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
             const float* tp = c.tg + rho;
+            float ring[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
+            tp += R * st;
             float p[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) p[w] = a[w * st];
-            float tv = __ldg(tp);
-            tp += st;
             const float* an = a + W * st;
             int jj = 0;
             for (; jj + W <= jrows; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
-                    const float tcur = tv;
-                    tv = __ldg(tp);
+                    const float tcur = ring[u % R];
+                    ring[u % R] = __ldg(tp);
                     tp += st;
 #pragma unroll
                     for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
@@ -291,8 +315,8 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
 #pragma unroll
             for (int u = 0; u < W; ++u) {
                 if (jj + u >= jrows) break;
-                const float tcur = tv;
-                tv = __ldg(tp);
+                const float tcur = ring[u % R];
+                ring[u % R] = __ldg(tp);
                 tp += st;
 #pragma unroll
                 for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
