@@ -487,6 +487,10 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
                     t.tasks = (nwin + t.per_task - 1) / t.per_task;
                     const int jrows = (t.d + t.st - 1) / t.st;
                     t.jrows = jrows;
+                    t.toff = dp.tmpl_off[j];
+                    t.t2off = dp.tmpl2_off[j];
+                    t.inv_sum_t = dp.inv_sum_t[j] * (1.0f / 1099511627776.0f);  // 2^-40 fixed point
+                    t.sum_t2 = dp.sum_t2[j];
                     // rows up to m + w + jrows - 1 and columns up to st + 31 must stay in the buffer
                     const int m_max_start = (x0 + tc.buf - 32) / t.st - t.w - jrows;
                     t.hi_start = min(t.m_total - t.w, m_max_start);
@@ -537,27 +541,23 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             c.nc = t.nc;
             c.lg_nc = __ffs(t.nc) - 1;
             c.jrows = t.jrows;
-            c.tg2 = dp.tmpl2 + dp.tmpl2_off[t.j];
+            c.tg2 = dp.tmpl2 + t.t2off;
             c.m_first = t.m_a + (task - t.first) * t.per_task;
             c.m_a = t.m_a;
             c.m_b = t.m_b;
             c.hi_start = t.hi_start;
             c.m_total = t.m_total;
-            c.tg = dp.tmpl + dp.tmpl_off[t.j];
-            c.inv_sum_t = dp.inv_sum_t[t.j] * (1.0f / 1099511627776.0f);  // 2^-40 fixed point
-            c.sum_t2 = dp.sum_t2[t.j];
+            c.tg = dp.tmpl + t.toff;
+            c.inv_sum_t = t.inv_sum_t;
+            c.sum_t2 = t.sum_t2;
             c.w_uni = w_uni;
             c.j = t.j;
             c.pf = dk.pf + (int64_t)slot * dk.pad_stride;
             switch (t.variant) {
             case kWin16: warp_task_winpair<16, 4>(c, lane, best); break;
-            case kWin14: warp_task_winpair<14, 7>(c, lane, best); break;
-            case kWin12: warp_task_winpair<12, 6>(c, lane, best); break;
-            case kWin8: warp_task_winpair<8, 4>(c, lane, best); break;
             case kCol16: warp_task_colpair<16, 4>(c, lane, best); break;
             case kCol15: warp_task_colpair<15, 5>(c, lane, best); break;
             case kCol12: warp_task_colpair<12, 4>(c, lane, best); break;
-            case kCol8: warp_task_colpair<8, 4>(c, lane, best); break;
             default: warp_task_scalar<15, 5>(c, lane, best); break;
             }
         }
@@ -867,27 +867,16 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
         }
         return std::min(1.0, 0.85 * pipe / slots);
     };
+    // variants built into the kernel: scalar15 (nc = 2^v), winpair16 (nc = 32),
+    // colpair 16 / 15 / 12 (W st = nc * odd)
     consider(tiles::kWin16, 32, ipc(tiles::kWin16));
     consider(tiles::kCol16, 32, ipc(tiles::kCol16));
     if (v <= 4) {
         consider(tiles::kScalar15, 1 << v, ipc(tiles::kScalar15));
         consider(tiles::kCol15, 1 << v, ipc(tiles::kCol15));
     }
-    if (v + 1 <= 5) {
-        consider(tiles::kWin14, 1 << (v + 1), ipc(tiles::kWin14));
-    }
-    if (v + 2 <= 5) {
-        consider(tiles::kWin12, 1 << (v + 2), ipc(tiles::kWin12));
-        consider(tiles::kCol12, 1 << (v + 2), ipc(tiles::kCol12));
-    }
-    if (v + 3 <= 5) {
-        consider(tiles::kWin8, 1 << (v + 3), ipc(tiles::kWin8));
-        consider(tiles::kCol8, 1 << (v + 3), ipc(tiles::kCol8));
-    }
-    if (v + 4 <= 5) {
-        consider(tiles::kWin16, 1 << (v + 4), ipc(tiles::kWin16));
-        consider(tiles::kCol16, 1 << (v + 4), ipc(tiles::kCol16));
-    }
+    if (v + 2 <= 5) consider(tiles::kCol12, 1 << (v + 2), ipc(tiles::kCol12));
+    if (v + 4 <= 5) consider(tiles::kCol16, 1 << (v + 4), ipc(tiles::kCol16));
 }
 
 int fold_smem_bytes(int bucket_log2)
@@ -1003,7 +992,7 @@ gtls_status create_device(gtls_plan* pl)
         const int static_bytes = 8192;  // duration table and reduction scratch, rounded up
         // floats of folded curve staged per tile; the rest of the SM's
         // unified L1/shared memory caches the template tables
-        int want = 32768;
+        int want = 49152;
         if (const char* e = std::getenv("GTLS_TILE_FLOATS")) want = std::max(4096, std::atoi(e));
         int buf = std::min(want, (smem_optin - static_bytes) / 4) & ~63;
         {

@@ -23,15 +23,20 @@
 //   Variants (chosen per duration when the plan is made):
 //     colpair<W>  one FFMA2 per window covers the two columns rho, rho + nc
 //                 (template pairs come from a per-duration pair table whose
-//                 second value is zero where rho + nc >= st);
-//     winpair<W>  one FFMA2 covers windows w and w + W/2 of one column;
-//     scalar<15>  plain FFMA (strides that are small powers of two).
+//                 second value is zero where rho + nc >= st);  W = 16, 15, 12
+//     winpair<16> one FFMA2 covers windows w and w + 8 of one column
+//                 (T0 steps that are multiples of 32);
+//     scalar<15>  plain FFMA (T0 steps 1, 2, 4, 8, 16).
+//   Each variant is one unrolled loop of W rows (a uniform exit test per
+//   row), which keeps the kernel's code small enough for the instruction
+//   caches.
 //   Templates are followed by zeros, so every lane runs the same J steps
 //   and template rows can be fetched several rows ahead (register ring).
-//   The nc lanes of a block add their partial sums with a butterfly; each
-//   lane then finishes W / nc windows and keeps a packed running minimum
-//   (delta-chi2 key, duration index, window index), merged per period with
-//   one 64-bit atomicMin.
+//   The nc lanes of a block combine their partial sums by recursive halving
+//   (each exchange halves the values a lane holds), so every lane ends with
+//   exactly its W / nc windows, finishes them and keeps a packed running
+//   minimum (delta-chi2 key, duration index, window index), merged per
+//   period with one 64-bit atomicMin.
 #pragma once
 
 namespace gtls {
@@ -76,6 +81,8 @@ __host__ __device__ inline bool variant_colpair(int v) { return v >= kCol16; }
 
 struct DurTask {
     int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total, jrows;
+    long long toff, t2off;    // template offsets (floats / float2 pairs)
+    float inv_sum_t, sum_t2;  // 2^-40 / sum_k s_k and sum_k s_k^2
 };
 
 struct WinCtx {
@@ -112,23 +119,51 @@ __device__ __forceinline__ unsigned long long finish_window(const WinCtx& c, lon
     return ((unsigned long long)u << 32) | ((unsigned long long)c.j << 24) | (unsigned long long)m;
 }
 
-// Butterfly over the nc lanes of a block, then lane c finishes the windows
-// w with w mod nc == c.
+// One recursive-halving exchange over lane bit `o`: the lane keeps the lower
+// (bit clear) or upper (bit set) half of its CNT values, adds the partner's
+// copy of that half, and sends the other half.
+template <int CNT>
+__device__ __forceinline__ void halve(float (&v)[16], int lane, int o, int& base)
+{
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < CNT / 2; ++i) {
+        const float send = up ? v[i] : v[i + CNT / 2];
+        const float keep = up ? v[i + CNT / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (up) base += CNT / 2;
+}
+
+// Combine the nc = 2^lg_nc partial sums of a block (lanes b*nc .. b*nc+nc-1)
+// and finish this lane's windows mb + base .. mb + base + cnt - 1.
 template <int W>
-__device__ __forceinline__ void reduce_finish(const WinCtx& c, float (&tot)[W], int mb, bool active,
+__device__ __forceinline__ void reduce_finish(const WinCtx& c, const float (&tot)[W], int mb, bool active,
                                               int lane, unsigned long long& best)
 {
-    for (int o = 1; o < c.nc; o <<= 1) {
+    static_assert(W <= 16, "at most 16 windows per block");
+    float v[16];
 #pragma unroll
-        for (int w = 0; w < W; ++w) tot[w] += __shfl_xor_sync(0xffffffffu, tot[w], o);
-    }
-    const int cc = lane & (c.nc - 1);
+    for (int i = 0; i < 16; ++i) v[i] = i < W ? tot[i] : 0.0f;
+    const int k = c.lg_nc;
+    int base = 0;
+    if (k >= 1) halve<16>(v, lane, 1, base);
+    if (k >= 2) halve<8>(v, lane, 2, base);
+    if (k >= 3) halve<4>(v, lane, 4, base);
+    if (k >= 4) halve<2>(v, lane, 8, base);
+    if (k >= 5) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);   // lanes 16..31 repeat 0..15
+    const int cnt = 16 >> min(k, 4);
+    if (!active || (k >= 5 && (lane & 16))) return;
+    float e[16];   // this lane's window totals, walked with a runtime count
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
+    for (int i = 0; i < 16; ++i) e[i] = v[i];
+#pragma unroll 4
+    for (int i = 0; i < cnt; ++i) {
+        const int w = base + i;
         const int m = mb + w;
-        if (active && (w & (c.nc - 1)) == cc && m < c.m_total) {
-            const unsigned long long k = finish_window(c, m, tot[w]);
-            best = k < best ? k : best;
+        if (w < W && m < c.m_total) {
+            const unsigned long long key = finish_window(c, m, e[i]);
+            best = key < best ? key : best;
         }
     }
 }
@@ -170,10 +205,10 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
                 p[w].y = a[w * st + nc];
             }
             const float* an = a + W * st;
-            int jj = 0;
-            for (; jj + W <= jrows; jj += W) {
+            for (int jj = 0; jj < jrows; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
+                    if (jj + u >= jrows) break;
                     const float2 tcur = ring[u % R];
                     ring[u % R] = __ldg(tp);     // row jj + u + R (zero padded past D)
                     tp += st;
@@ -183,18 +218,6 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
                     p[u].y = an[nc];
                     an += st;
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                if (jj + u >= jrows) break;
-                const float2 tcur = ring[u % R];
-                ring[u % R] = __ldg(tp);
-                tp += st;
-#pragma unroll
-                for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
-                p[u].x = an[0];
-                p[u].y = an[nc];
-                an += st;
             }
         }
     }
@@ -235,10 +258,10 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
                 p[w].y = a[(w + H) * st];
             }
             const float* an = a + W * st;
-            int jj = 0;
-            for (; jj + H <= jrows; jj += H) {
+            for (int jj = 0; jj < jrows; jj += H) {
 #pragma unroll
                 for (int u = 0; u < H; ++u) {
+                    if (jj + u >= jrows) break;
                     const float tv = ring[u % R];
                     ring[u % R] = __ldg(tp);
                     tp += st;
@@ -249,19 +272,6 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
                     p[u].y = *an;
                     an += st;
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < H; ++u) {
-                if (jj + u >= jrows) break;
-                const float tv = ring[u % R];
-                ring[u % R] = __ldg(tp);
-                tp += st;
-                const float2 t2 = make_float2(tv, tv);
-#pragma unroll
-                for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
-                p[u].x = p[u].y;
-                p[u].y = *an;
-                an += st;
             }
         }
     }
@@ -299,10 +309,10 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
 #pragma unroll
             for (int w = 0; w < W; ++w) p[w] = a[w * st];
             const float* an = a + W * st;
-            int jj = 0;
-            for (; jj + W <= jrows; jj += W) {
+            for (int jj = 0; jj < jrows; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
+                    if (jj + u >= jrows) break;
                     const float tcur = ring[u % R];
                     ring[u % R] = __ldg(tp);
                     tp += st;
@@ -311,17 +321,6 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
                     p[u] = *an;
                     an += st;
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                if (jj + u >= jrows) break;
-                const float tcur = ring[u % R];
-                ring[u % R] = __ldg(tp);
-                tp += st;
-#pragma unroll
-                for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
-                p[u] = *an;
-                an += st;
             }
         }
     }
