@@ -455,13 +455,6 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
         // stage the folded, padded curve [x0, x0 + buf) (zeros past its end)
         const float* src = dk.rs + (int64_t)slot * dk.pad_stride + x0;
         const int valid = (int)min((int64_t)tc.buf, n + (int64_t)dp.dmax_p[p] + kPadMargin - x0);
-        if (threadIdx.x == 0) {
-            // bring the tile's prefix sums (read by the window epilogues) into L2
-            const long long* pfs = dk.pf + (int64_t)slot * dk.pad_stride + x0;
-            const int64_t want = min((int64_t)tc.len + dp.dmax_p[p] + 64, n + (int64_t)dp.dmax_p[p] + 1 - x0);
-            const unsigned int bytes = (unsigned int)((want * 8 + 15) & ~int64_t(15));
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pfs), "r"(bytes) : "memory");
-        }
         const int v4 = valid >> 2;
         for (int i = threadIdx.x; i < v4; i += blockDim.x)
             reinterpret_cast<float4*>(tile_smem)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);

@@ -175,37 +175,6 @@ __device__ __forceinline__ int block_start(const WinCtx& c, int b, int w, bool& 
     return max(c.m_a, min(m0, c.hi_start));
 }
 
-// First window (within its block) that recursive halving leaves to this lane.
-__device__ __forceinline__ int lane_window_base(int lane, int k)
-{
-    int base = 0;
-    if (k >= 1 && (lane & 1)) base += 8;
-    if (k >= 2 && (lane & 2)) base += 4;
-    if (k >= 3 && (lane & 4)) base += 2;
-    if (k >= 4 && (lane & 8)) base += 1;
-    return base;
-}
-
-// Ask L1 for the prefix-sum entries this lane's windows will read after the
-// FMA loop, so the epilogue does not wait on memory.
-template <int W>
-__device__ __forceinline__ void prefetch_window_sums(const WinCtx& c, int mb, bool active, int lane)
-{
-    const int k = c.lg_nc;
-    if (!active || (k >= 5 && (lane & 16))) return;
-    const int base = lane_window_base(lane, k);
-    const int cnt = 16 >> min(k, 4);
-    for (int i = 0; i < cnt; ++i) {
-        const int w = base + i;
-        const int m = mb + w;
-        if (w < W && m < c.m_total) {
-            const long long s = (long long)m * c.st;
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(c.pf + s));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(c.pf + s + c.d));
-        }
-    }
-}
-
 // Column pairs: acc[w] = (column rho, column rho + nc) partial sums of window w.
 // Template rows are fetched R rows ahead into a register ring (R divides W).
 template <int W, int R>
@@ -217,7 +186,6 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
     bool active;
     const int mb = block_start(c, b, W, active);
     const int st = c.st, nc = c.nc, jrows = c.jrows;
-    prefetch_window_sums<W>(c, mb, active, lane);
     float2 acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = make_float2(0.0f, 0.0f);
@@ -271,7 +239,6 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
     bool active;
     const int mb = block_start(c, b, W, active);
     const int st = c.st, jrows = c.jrows;
-    prefetch_window_sums<W>(c, mb, active, lane);
     float2 acc[H];
 #pragma unroll
     for (int w = 0; w < H; ++w) acc[w] = make_float2(0.0f, 0.0f);
@@ -326,7 +293,6 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
     bool active;
     const int mb = block_start(c, b, W, active);
     const int st = c.st, jrows = c.jrows;
-    prefetch_window_sums<W>(c, mb, active, lane);
     float acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = 0.0f;
