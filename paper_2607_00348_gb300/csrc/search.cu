@@ -490,6 +490,7 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
                     t.toff = dp.tmpl_off[j];
                     t.t2off = dp.tmpl2_off[j];
                     t.inv_sum_t = dp.inv_sum_t[j] * (1.0f / 1099511627776.0f);  // 2^-40 fixed point
+                    t.inv_sum_t_f = dp.inv_sum_t[j];
                     t.sum_t2 = dp.sum_t2[j];
                     // rows up to m + w + jrows - 1 and columns up to st + 31 must stay in the buffer
                     const int m_max_start = (x0 + tc.buf - 32) / t.st - t.w - jrows;
@@ -530,8 +531,13 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             if (lane == 0) task = atomicAdd(&s_task, 1);
             task = __shfl_sync(0xffffffffu, task, 0);
             if (task >= total) break;
-            int k = 0;
-            while (k + 1 < ndur && dur[k + 1].first <= task) ++k;
+            int lo_k = 0, hi_k = ndur - 1;   // last entry with first <= task
+            while (lo_k < hi_k) {
+                const int mid = (lo_k + hi_k + 1) >> 1;
+                if (dur[mid].first <= task) lo_k = mid;
+                else hi_k = mid - 1;
+            }
+            const int k = lo_k;
             const DurTask t = dur[k];
             WinCtx c;
             c.tile = tile_smem;
@@ -549,6 +555,7 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             c.m_total = t.m_total;
             c.tg = dp.tmpl + t.toff;
             c.inv_sum_t = t.inv_sum_t;
+            c.inv_sum_t_f = t.inv_sum_t_f;
             c.sum_t2 = t.sum_t2;
             c.w_uni = w_uni;
             c.j = t.j;
@@ -856,8 +863,8 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
         const int w = tiles::variant_w(var);
         double pipe, slots;
         if (var == tiles::kScalar15) {
-            pipe = w;
-            slots = w + 5;
+            pipe = w;            // half of the FFMA2 work is the window sum S
+            slots = w + 6;
         } else if (tiles::variant_colpair(var)) {
             pipe = 2.0 * w;
             slots = w + 6;
@@ -1033,10 +1040,20 @@ gtls_status create_device(gtls_plan* pl)
                 const int nwin = (int)std::min<int64_t>(m_total, (len + st - 1) / st);
                 pick_config_host(st, nwin, var[j], ncs[j]);
                 off2[j] = pos2;
-                if (tiles::variant_colpair(var[j])) pos2 += h.dpts[j] + (tiles::kMaxRing + 2) * (int64_t)st + 64;
+                if (tiles::variant_colpair(var[j]) || var[j] == tiles::kScalar15)
+                    pos2 += h.dpts[j] + (tiles::kMaxRing + 2) * (int64_t)st + 64;
             }
             t2.assign((size_t)std::max<int64_t>(pos2, 1), make_float2(0.0f, 0.0f));
             for (int j = 0; j < dp.nd; ++j) {
+                if (var[j] == tiles::kScalar15) {
+                    // (s_k, 1): one FFMA2 gives C1 and the window sum S
+                    const int st = h.stride[j], d = h.dpts[j];
+                    const float* tj = pl->tmpl_pad.data() + pl->tmpl_pad_off[j];
+                    const int64_t len2 = d + (tiles::kMaxRing + 2) * (int64_t)st + 64;
+                    for (int64_t k = 0; k < len2; ++k)
+                        t2[(size_t)(off2[j] + k)] = k < d ? make_float2(tj[k], 1.0f) : make_float2(0.0f, 0.0f);
+                    continue;
+                }
                 if (!tiles::variant_colpair(var[j])) continue;
                 const int st = h.stride[j], d = h.dpts[j], nc = ncs[j];
                 const float* tj = pl->tmpl_pad.data() + pl->tmpl_pad_off[j];

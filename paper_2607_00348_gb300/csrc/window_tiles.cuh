@@ -26,7 +26,8 @@
 //                 second value is zero where rho + nc >= st);  W = 16, 15, 12
 //     winpair<16> one FFMA2 covers windows w and w + 8 of one column
 //                 (T0 steps that are multiples of 32);
-//     scalar<15>  plain FFMA (T0 steps 1, 2, 4, 8, 16).
+//     scalar<15>  T0 steps 1, 2, 4, 8, 16 (one column per lane): each FFMA2
+//                 accumulates (C1, S) of one window from a (s_k, 1) table.
 //   Each variant is one unrolled loop of W rows (a uniform exit test per
 //   row), which keeps the kernel's code small enough for the instruction
 //   caches.
@@ -83,6 +84,7 @@ struct DurTask {
     int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total, jrows;
     long long toff, t2off;    // template offsets (floats / float2 pairs)
     float inv_sum_t, sum_t2;  // 2^-40 / sum_k s_k and sum_k s_k^2
+    float inv_sum_t_f;        // 1 / sum_k s_k
 };
 
 struct WinCtx {
@@ -94,6 +96,7 @@ struct WinCtx {
     const float* tg;          // template of the duration (global, zero padded)
     const float2* tg2;        // template pairs (colpair variants)
     float inv_sum_t, sum_t2, w_uni;
+    float inv_sum_t_f;        // 1 / sum_k s_k (no fixed-point scale)
     int j;
     const long long* pf;      // prefix sums of the period (global)
 };
@@ -168,6 +171,60 @@ __device__ __forceinline__ void reduce_finish(const WinCtx& c, const float (&tot
     }
 }
 
+template <int CNT>
+__device__ __forceinline__ void halve2(float2 (&v)[16], int lane, int o, int& base)
+{
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < CNT / 2; ++i) {
+        const float2 send = up ? v[i] : v[i + CNT / 2];
+        const float2 keep = up ? v[i + CNT / 2] : v[i];
+        v[i].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, o);
+        v[i].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, o);
+    }
+    if (up) base += CNT / 2;
+}
+
+// As reduce_finish for (C1, S) pairs: the window sum comes with C1, so the
+// epilogue reads no prefix sums.
+template <int W>
+__device__ __forceinline__ void reduce_pair_finish(const WinCtx& c, const float2 (&tot)[W], int mb, bool active,
+                                                   int lane, unsigned long long& best)
+{
+    static_assert(W <= 16, "at most 16 windows per block");
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < W ? tot[i] : make_float2(0.0f, 0.0f);
+    const int k = c.lg_nc;
+    int base = 0;
+    if (k >= 1) halve2<16>(v, lane, 1, base);
+    if (k >= 2) halve2<8>(v, lane, 2, base);
+    if (k >= 3) halve2<4>(v, lane, 4, base);
+    if (k >= 4) halve2<2>(v, lane, 8, base);
+    if (k >= 5) {
+        v[0].x += __shfl_xor_sync(0xffffffffu, v[0].x, 16);
+        v[0].y += __shfl_xor_sync(0xffffffffu, v[0].y, 16);
+    }
+    const int cnt = 16 >> min(k, 4);
+    if (!active || (k >= 5 && (lane & 16))) return;
+    float2 e[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) e[i] = v[i];
+    for (int i = 0; i < cnt; ++i) {
+        const int w = base + i;
+        const int m = mb + w;
+        if (w < W && m < c.m_total) {
+            const float depth = fmaxf(0.0f, e[i].y * c.inv_sum_t_f);
+            const float dchi = c.w_uni * depth * fmaf(depth, c.sum_t2, -2.0f * e[i].x);
+            unsigned int u = __float_as_uint(dchi);
+            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            const unsigned long long key =
+                ((unsigned long long)u << 32) | ((unsigned long long)c.j << 24) | (unsigned long long)m;
+            best = key < best ? key : best;
+        }
+    }
+}
+
 __device__ __forceinline__ int block_start(const WinCtx& c, int b, int w, bool& active)
 {
     const int m0 = c.m_first + b * w;
@@ -191,13 +248,18 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
     for (int w = 0; w < W; ++w) acc[w] = make_float2(0.0f, 0.0f);
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
+        float2 nxt[R];   // first R template rows of the coming column round
+#pragma unroll
+        for (int r = 0; r < R; ++r) nxt[r] = __ldg(c.tg2 + cl + r * st);
         for (int rho = cl; rho < st; rho += 2 * nc) {
             const float* a = abase + rho;
-            const float2* tp = c.tg2 + rho;
             float2 ring[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
-            tp += R * st;
+            for (int r = 0; r < R; ++r) {
+                ring[r] = nxt[r];
+                nxt[r] = __ldg(c.tg2 + rho + 2 * nc + r * st);   // next round (zero padded)
+            }
+            const float2* tp = c.tg2 + rho + R * st;
             float2 p[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -244,13 +306,18 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
     for (int w = 0; w < H; ++w) acc[w] = make_float2(0.0f, 0.0f);
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
+        float nxt[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) nxt[r] = __ldg(c.tg + cl + r * st);
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            const float* tp = c.tg + rho;
             float ring[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
-            tp += R * st;
+            for (int r = 0; r < R; ++r) {
+                ring[r] = nxt[r];
+                nxt[r] = __ldg(c.tg + rho + c.nc + r * st);
+            }
+            const float* tp = c.tg + rho + R * st;
             float2 p[H];
 #pragma unroll
             for (int w = 0; w < H; ++w) {
@@ -284,6 +351,10 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
     reduce_finish<W>(c, tot, mb, active, lane, best);
 }
 
+// Small T0 steps (st = nc = 1, 2, 4, 8, 16): one column per lane.  Each
+// FFMA2 accumulates (C1, S) = (sum r s_k, sum r) of one window and column
+// from the pair table (s_k, 1); the nc columns are then combined, so the
+// window sum needs no prefix-sum reads.
 template <int W, int R>
 __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& best)
 {
@@ -293,38 +364,42 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
     bool active;
     const int mb = block_start(c, b, W, active);
     const int st = c.st, jrows = c.jrows;
-    float acc[W];
+    float2 acc[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) acc[w] = 0.0f;
+    for (int w = 0; w < W; ++w) acc[w] = make_float2(0.0f, 0.0f);
     if (active) {
         const float* abase = c.tile + (mb * st - c.x0);
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            const float* tp = c.tg + rho;
-            float ring[R];
+            const float2* tp = c.tg2 + rho;
+            float2 ring[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
             tp += R * st;
-            float p[W];
+            float2 p[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) p[w] = a[w * st];
+            for (int w = 0; w < W; ++w) {
+                const float v = a[w * st];
+                p[w] = make_float2(v, v);
+            }
             const float* an = a + W * st;
             for (int jj = 0; jj < jrows; jj += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     if (jj + u >= jrows) break;
-                    const float tcur = ring[u % R];
+                    const float2 tcur = ring[u % R];
                     ring[u % R] = __ldg(tp);
                     tp += st;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = fmaf(p[(w + u) % W], tcur, acc[w]);
-                    p[u] = *an;
+                    for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+                    const float v = *an;
+                    p[u] = make_float2(v, v);
                     an += st;
                 }
             }
         }
     }
-    reduce_finish<W>(c, acc, mb, active, lane, best);
+    reduce_pair_finish<W>(c, acc, mb, active, lane, best);
 }
 
 }  // namespace tiles
