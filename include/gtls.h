@@ -198,6 +198,31 @@ gtls_status gtls_plan_set_profiling(gtls_plan* plan, int32_t on);
 /* Stage times and launch counts of the plan's last search (host struct). */
 gtls_status gtls_plan_get_profile(const gtls_plan* plan, gtls_profile* out);
 
+/*
+ * SR, SDE_raw, SDE and the SDE argmax of a chi2(P) spectrum without any
+ * device allocation.  (The paper has no counterpart: this exists for callers
+ * that cannot call cudaMalloc, e.g. code confined to a pre-sized memory pool
+ * or to buffers handed over by another framework.)  Its scratch lives in a
+ * fixed device array compiled into the library: 2^19 trial periods at most
+ * (8 MiB plus a small header, held by every GPU that loads the library until
+ * the process exits); larger inputs return GTLS_ERR_INVALID_ARG.
+ *   chi2       device, n_periods doubles (input, read only)
+ *   sr_out, sde_raw_out   device, n_periods doubles each, nullable (then
+ *              kept in the fixed array)
+ *   sde_out    device, n_periods doubles (required)
+ *   best_idx, best_sde    host, nullable: first index of the largest SDE
+ *   median_window         0 => 2 floor(N_P/200) + 1, else odd
+ * The computation is the one gtls_search applies to its own chi2(P).
+ * The first call on a device looks up the array's device address (with
+ * cudaGetSymbolAddress) and sets a kernel attribute; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents, so calls that overlap on the GPU (different
+ * streams, or threads) race; serialise them.  Synchronises `stream`.
+ */
+gtls_status gtls_sr_sde_noalloc(const double* chi2, int64_t n_periods, int32_t median_window,
+                                void* stream, double* sr_out, double* sde_raw_out, double* sde_out,
+                                int64_t* best_idx, double* best_sde);
+
 /* Release the plan's device and host memory (NULL is a no-op). */
 void gtls_plan_destroy(gtls_plan* plan);
 

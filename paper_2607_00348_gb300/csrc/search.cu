@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1401,3 +1402,130 @@ const char* gtls_status_string(gtls_status s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free SR / SDE reduction
+// ---------------------------------------------------------------------------
+//
+// For callers that cannot allocate device memory (for example code running
+// inside a pre-sized memory pool, or a host process that hands all of its
+// allocations to another framework): the reduction of Sect. 2.4 over a
+// caller-owned chi2(P) spectrum, with its scratch (statistics, check words,
+// argmax, and SR / SDE_raw when the caller passes no buffer for them) in a
+// fixed file-scope device array instead of memory from cudaMalloc.  Every
+// GPU that loads this library holds the array until the process exits.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxPeriods = int64_t(1) << 19;  // 524,288 trial periods
+constexpr int64_t kNoAllocHead = 32;                        // doubles before the SR / SDE_raw areas
+// [0..4) stats  [4..8) check words  [8] best SDE  [9] best index (bits)
+// [32 .. 32+max) SR   [32+max .. 32+2 max) SDE_raw
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocHead + 2 * kNoAllocMaxPeriods];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64] = {};   // device address of g_noalloc_scratch per device
+
+__global__ void __launch_bounds__(1024) k_argmax_noalloc(int np, const double* __restrict__ sde, double* head)
+{
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    double v = -INFINITY;
+    int idx = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const double x = sde[i];
+        if (x > v) {
+            v = x;
+            idx = i;
+        }
+    }
+    bv[threadIdx.x] = v;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double ov = bv[threadIdx.x + s];
+            const int oi = bi[threadIdx.x + s];
+            if (ov > bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                bv[threadIdx.x] = ov;
+                bi[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        head[8] = bv[0];
+        head[9] = __longlong_as_double((long long)bi[0]);
+    }
+}
+
+// Device address of the scratch array on the current device; the first call
+// on a device looks it up (and sets the median kernel's shared-memory limit).
+gtls_status noalloc_scratch(int dev, double** out)
+{
+    if (dev < 0 || dev >= 64) return fail(GTLS_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        GTLS_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        GTLS_CUDA(cudaFuncSetAttribute(k_median_sde, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kMedianCap * (int)(sizeof(double) + sizeof(int))));
+        g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return GTLS_OK;
+}
+
+}  // namespace
+
+extern "C" gtls_status gtls_sr_sde_noalloc(const double* chi2, int64_t n_periods, int32_t median_window,
+                                           void* stream, double* sr_out, double* sde_raw_out, double* sde_out,
+                                           int64_t* best_idx, double* best_sde)
+{
+    g_last_error.clear();
+    if (!chi2 || !sde_out) return fail(GTLS_ERR_INVALID_ARG, "chi2 and sde_out are required");
+    if (n_periods < 1 || n_periods > kNoAllocMaxPeriods)
+        return fail(GTLS_ERR_INVALID_ARG, "n_periods must be in [1, " + std::to_string(kNoAllocMaxPeriods) +
+                                              "] for the allocation-free reduction");
+    if (median_window < 0 || (median_window > 0 && median_window % 2 == 0))
+        return fail(GTLS_ERR_INVALID_ARG, "median_window must be 0 or odd");
+    const int np = (int)n_periods;
+    const int win = median_window > 0 ? median_window : std::max(3, 2 * (np / 200) + 1);
+    const int hwin = win / 2;
+    const int outs = std::min(1024, kMedianCap - 2 * hwin) & ~31;
+    if (outs < 32) return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
+    int dev = -1;
+    GTLS_CUDA(cudaGetDevice(&dev));
+    double* head = nullptr;
+    GTLS_TRY(noalloc_scratch(dev, &head));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    DevPeriod dq{};
+    dq.chi2 = const_cast<double*>(chi2);
+    dq.sr = sr_out ? sr_out : head + kNoAllocHead;
+    dq.sde_raw = sde_raw_out ? sde_raw_out : head + kNoAllocHead + kNoAllocMaxPeriods;
+    dq.sde = sde_out;
+    dq.stats = head;
+    dq.check = reinterpret_cast<unsigned int*>(head + 4);
+    // the array keeps the previous call's contents: clear the check words
+    GTLS_CUDA(cudaMemsetAsync(head + 4, 0, 4 * sizeof(double), st));
+    k_sr_stats<<<1, 1024, 0, st>>>(np, dq);
+    GTLS_CUDA(cudaGetLastError());
+    k_median_sde<<<(np + outs - 1) / outs, kMedianThreads, kMedianCap * (int)(sizeof(double) + sizeof(int)), st>>>(
+        np, hwin, outs, dq);
+    GTLS_CUDA(cudaGetLastError());
+    k_argmax_noalloc<<<1, 1024, 0, st>>>(np, sde_out, head);
+    GTLS_CUDA(cudaGetLastError());
+    double res[2] = {0.0, 0.0};
+    unsigned int chk[4] = {0, 0, 0, 0};
+    GTLS_CUDA(cudaMemcpyAsync(res, head + 8, sizeof res, cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaMemcpyAsync(chk, head + 4, sizeof chk, cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaStreamSynchronize(st));
+    if (chk[0] != 0)
+        return fail(GTLS_ERR_INTERNAL, "device index check " + std::to_string(chk[0]) + " failed");
+    long long bidx = 0;
+    std::memcpy(&bidx, &res[1], sizeof bidx);
+    if (best_idx) *best_idx = bidx;
+    if (best_sde) *best_sde = res[0];
+    return GTLS_OK;
+}

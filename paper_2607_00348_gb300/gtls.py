@@ -104,6 +104,9 @@ SIGNATURES = [
                                          c_int64_p, ctypes.c_void_p, ctypes.POINTER(Result)]),
     ("gtls_plan_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("gtls_plan_get_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
+    ("gtls_sr_sde_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, c_int64_p, c_double_p]),
     ("gtls_plan_destroy", None, [ctypes.c_void_p]),
     ("gtls_last_error", ctypes.c_char_p, []),
     ("gtls_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -284,3 +287,20 @@ def search_batch(plans, t, y, dy, offsets, stream=None):
     _check(lib.gtls_search_batch(arr, n_lc, _ptr(t), _ptr(y), _ptr(dy),
                                  offs.ctypes.data_as(c_int64_p), _stream_handle(stream), out))
     return list(out)
+
+
+def sr_sde_noalloc(chi2, sde, sr=None, sde_raw=None, median_window=0, stream=None):
+    """gtls_sr_sde_noalloc on device tensors (float64); returns (best index, best SDE).
+
+    The reduction's scratch is a fixed array inside the library (no device
+    allocation by the call); `sde` (and `sr`, `sde_raw` when given) receive
+    the spectra.
+    """
+    lib = load()
+    bi = ctypes.c_int64(0)
+    bs = ctypes.c_double(0.0)
+    n = int(chi2.numel())
+    _check(lib.gtls_sr_sde_noalloc(_ptr(chi2), n, int(median_window), _stream_handle(stream),
+                                   _ptr(sr), _ptr(sde_raw), _ptr(sde), ctypes.byref(bi),
+                                   ctypes.byref(bs)))
+    return int(bi.value), float(bs.value)
