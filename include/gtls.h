@@ -73,6 +73,10 @@ typedef struct {
     int32_t periods_per_chunk;  /* periods folded per kernel wave; 0 => fit 2 GiB of scratch */
     const double* periods_days; /* optional explicit period grid (host, copied); NULL => Ofir */
     int64_t n_periods;          /* length of periods_days */
+    int32_t refine_periods;     /* K > 0: re-search the K best periods by SDE(P) with T0 step 1
+                                   (Sect. 2.5, two-stage T0 search), then recompute SR/SDE;
+                                   0 => coarse pass only (default) */
+    int32_t reserved1;
 } gtls_plan_params;
 
 /* Sizes of a plan (host struct filled by gtls_plan_get_info). */
@@ -104,7 +108,7 @@ typedef struct {
     int32_t dur_points;   /* D */
     int64_t t0_idx;       /* window start in folded order (multiple of the T0 step) */
     int32_t uniform_dy;   /* 1 if all dy were equal (uniform-weight kernel) */
-    int32_t reserved0;
+    int32_t refined;      /* number of periods re-searched with T0 step 1 */
 } gtls_result;
 
 /* Optional per-period outputs (device pointers, each nullable, n_periods long). */
@@ -117,6 +121,7 @@ typedef struct {
     double* sr;       /* SR(P) */
     double* sde_raw;  /* SDE_raw(P) */
     double* sde;      /* SDE(P) */
+    int32_t* refined; /* 1 where the period was re-searched with T0 step 1, else 0 */
 } gtls_period_outputs;
 
 /* Per-stage device time of the last search (host struct). */

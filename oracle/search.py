@@ -190,10 +190,36 @@ def sr_sde(chi2):
     return sr, raw, sde
 
 
-def full_search(p: OraclePlan, t, y, dy, n_threads=0):
-    """Every period, then SR/SDE and the best candidate (argmax SDE)."""
+def refine_selection(sde, k):
+    """The k periods with the largest SDE(P), ties by lower index (Sect. 2.5)."""
+    sde = np.asarray(sde, np.float64)
+    order = np.lexsort((np.arange(sde.size), -sde))
+    return np.sort(order[:k])
+
+
+def full_search(p: OraclePlan, t, y, dy, n_threads=0, refine_top_k=0):
+    """Every period, then SR/SDE and the best candidate (argmax SDE).
+
+    With refine_top_k = K > 0 the two-stage T0 search of Sect. 2.5 follows:
+    the K best periods by SDE(P) are searched again without skipping T0
+    points (step 1), their chi2(P) replace the coarse ones, and SR/SDE are
+    computed once more.
+    """
     r = search_periods(p, t, y, dy, None, n_threads)
     sr, raw, sde = sr_sde(r.chi2)
+    r.refined = np.zeros(r.chi2.size, dtype=bool)
+    if refine_top_k > 0:
+        sel = refine_selection(sde, min(refine_top_k, r.chi2.size))
+        p1 = dataclasses.replace(p, dt0=0.0)      # st = max(1, floor(D * 0)) = 1
+        r1 = search_periods(p1, t, y, dy, sel, n_threads)
+        r.chi2[sel] = r1.chi2
+        r.j_best[sel] = r1.j_best
+        r.s_best[sel] = r1.s_best
+        r.depth[sel] = r1.depth
+        r.rho_c[sel] = r1.rho_c
+        r.t0[sel] = r1.t0
+        r.refined[sel] = True
+        sr, raw, sde = sr_sde(r.chi2)
     b = int(np.argmax(sde))
     j = int(r.j_best[b])
     best = dict(period_idx=b, period=float(p.periods[b]), dur_idx=j,

@@ -85,6 +85,7 @@ struct DevPeriod {
     double* sde;
     double* stats;            // [0] chi2_min [1] mean SR [2] std SR
     unsigned int* check;      // same words as DevCurve::check
+    int32_t* refined;         // 1 where the period was re-searched with T0 step 1
     gtls_result* result;      // device copy of the best candidate
 };
 
@@ -106,6 +107,13 @@ struct gtls_plan {
     int tile_buf = 0, tile_len = 0, tile_count = 0;
     int n_sm = 0;
     unsigned int* tile_counter = nullptr;
+    // refinement stage (T0 step 1 on the best periods): plan tables with
+    // stride 1 and the (s_k, 1) pair tables, its tile configuration and the
+    // device list of periods to re-search
+    int refine_k = 0;
+    gtls::DevPlan dp_ref{};
+    int tile_len_ref = 0, tile_count_ref = 0;
+    int32_t* plist = nullptr;
     std::vector<float> tmpl_pad;        // host copy of the zero-padded template table
     std::vector<int64_t> tmpl_pad_off;
     // stage profiling: events recorded on the search stream when enabled
@@ -113,6 +121,6 @@ struct gtls_plan {
     std::vector<cudaEvent_t> events;
     std::vector<int> event_stage;   // stage of the interval ending at event i
     gtls_profile profile{};
-    void* allocs[64] = {};
+    void* allocs[96] = {};
     int n_allocs = 0;
 };

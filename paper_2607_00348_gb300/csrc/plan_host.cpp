@@ -62,6 +62,9 @@ bool build_plan_host(const gtls_plan_params& p, PlanHost& h, std::string& err)
     if (!(p.dur_ratio > 1.0) || !(p.dt0 > 0.0) || p.dt0 > 1.0) {
         err = "need dur_ratio > 1 and 0 < dt0 <= 1"; return false;
     }
+    if (p.refine_periods < 0 || p.refine_periods > 65535) {
+        err = "refine_periods must be in [0, 65535]"; return false;
+    }
     if (p.periods_per_chunk < 0 || p.periods_per_chunk > 65535) {
         err = "periods_per_chunk must be in [0, 65535]"; return false;
     }

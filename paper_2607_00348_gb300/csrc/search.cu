@@ -229,7 +229,7 @@ __global__ void k_curve_reduce(int nparts, const double* __restrict__ dy, DevCur
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kFoldThreads)
-k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
+k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, const int32_t* plist)
 {
     extern __shared__ unsigned char smem[];
     const int nb = 1 << dp.bucket_log2;
@@ -239,7 +239,7 @@ k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
     long long* total = warp_sums + 32;
 
     const int slot_id = blockIdx.x;
-    const int p = p0 + slot_id;
+    const int p = plist ? plist[slot_id] : p0 + slot_id;
     if (p >= dp.np) return;
     const int64_t n = dp.n;
     const long long P = dp.p_lat[p];
@@ -363,11 +363,11 @@ __device__ __forceinline__ int kept_j(const DevPlan& dp, int p, int slot)
 }
 
 __global__ void __launch_bounds__(kSearchThreads)
-k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0)
+k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, const int32_t* plist)
 {
     __shared__ unsigned long long red[kSearchThreads / 32];
     const int slot_id = blockIdx.z;
-    const int p = p0 + slot_id;
+    const int p = plist ? plist[slot_id] : p0 + slot_id;
     if (p >= dp.np) return;
     const int j = kept_j(dp, p, blockIdx.y);
     if (j < 0) return;
@@ -433,7 +433,7 @@ struct TileCfg {
 
 __global__ void __launch_bounds__(tiles::kThreads, 1)
 k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, int p0, int cnt,
-               unsigned int* counter)
+               unsigned int* counter, const int32_t* plist)
 {
     using namespace tiles;
     extern __shared__ float tile_smem[];
@@ -450,7 +450,7 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
         const int item = s_item;
         if (item >= items) break;
         const int slot = item / tc.tiles, tau = item - (item / tc.tiles) * tc.tiles;
-        const int p = p0 + slot;
+        const int p = plist ? plist[slot] : p0 + slot;
         const int x0 = tau * tc.len;
 
         // stage the folded, padded curve [x0, x0 + buf) (zeros past its end)
@@ -588,11 +588,12 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
 // per-period result: chi2(P), depth, T0 of the minimum
 // ---------------------------------------------------------------------------
 
-__global__ void k_period_finalize(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, int cnt)
+__global__ void k_period_finalize(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, int cnt,
+                                  const int32_t* plist)
 {
     const int slot_id = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot_id >= cnt) return;
-    const int p = p0 + slot_id;
+    const int p = plist ? plist[slot_id] : p0 + slot_id;
     if (p >= dp.np) return;
     const unsigned long long b = dq.best[p];
     const float dchi = float_from_order_key((unsigned int)(b >> 32));
@@ -741,6 +742,56 @@ __global__ void __launch_bounds__(kMedianThreads) k_median_sde(int np, int h, in
     }
 }
 
+// The k periods with the largest SDE (ties: lower index first), in rank
+// order, into plist; flags them in dq.refined.  One block, k argmax passes
+// over the periods not yet taken (a bit mask in shared memory).
+__global__ void __launch_bounds__(1024) k_topk(int np, int k, DevPeriod dq, int32_t* plist)
+{
+    extern __shared__ unsigned int taken[];
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    const int words = (np + 31) >> 5;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) taken[w] = 0u;
+    __syncthreads();
+    for (int r = 0; r < k; ++r) {
+        double v = -INFINITY;
+        int idx = 0x7fffffff;
+        for (int i = threadIdx.x; i < np; i += blockDim.x) {
+            if (taken[i >> 5] & (1u << (i & 31))) continue;
+            const double x = dq.sde[i];
+            if (x > v || (x == v && i < idx)) {
+                v = x;
+                idx = i;
+            }
+        }
+        bv[threadIdx.x] = v;
+        bi[threadIdx.x] = idx;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double ov = bv[threadIdx.x + s];
+                const int oi = bi[threadIdx.x + s];
+                if (ov > bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                    bv[threadIdx.x] = ov;
+                    bi[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const int b = bi[0];
+            if (in_range(dq.check, 21, b, np)) {
+                plist[r] = b;
+                taken[b >> 5] |= 1u << (b & 31);
+                dq.refined[b] = 1;
+            } else {
+                plist[r] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPeriod dq)
 {
     __shared__ double bv[1024];
@@ -787,7 +838,7 @@ __global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPerio
         r.dur_points = dp.dpts[j];
         r.t0_idx = dq.t0i[b];
         r.uniform_dy = dc.scal[2] > 0.0 ? 1 : 0;
-        r.reserved0 = 0;
+        r.refined = 0;
         *dq.result = r;
     }
 }
@@ -1072,6 +1123,46 @@ gtls_status create_device(gtls_plan* pl)
         GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl2_off), off2));
         if (t2.empty()) t2.assign(1, make_float2(0.0f, 0.0f));
         GTLS_TRY(upload(pl, const_cast<float2**>(&dp.tmpl2), t2));
+
+        // refinement stage: every duration with T0 step 1 through the (C1, S)
+        // variant (one column per lane)
+        pl->refine_k = std::min<int>(h.prm.refine_periods, dp.np);
+        GTLS_TRY(dev_alloc(pl, &pl->dq.refined, dp.np));
+        if (pl->refine_k > 0) {
+            pl->dp_ref = dp;
+            std::vector<int32_t> ones(dp.nd, 1), var1(dp.nd, tiles::kScalar15);
+            std::vector<int64_t> off1(dp.nd);
+            int64_t pos1 = 0;
+            for (int j = 0; j < dp.nd; ++j) {
+                off1[j] = pos1;
+                pos1 += h.dpts[j] + (tiles::kMaxRing + 2) + 64;
+            }
+            std::vector<float2> t21((size_t)pos1, make_float2(0.0f, 0.0f));
+            for (int j = 0; j < dp.nd; ++j) {
+                const float* tj = pl->tmpl_pad.data() + pl->tmpl_pad_off[j];
+                for (int k = 0; k < h.dpts[j]; ++k) t21[(size_t)(off1[j] + k)] = make_float2(tj[k], 1.0f);
+            }
+            GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.stride), ones));
+            GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_variant), var1));
+            GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_nc), ones));
+            GTLS_TRY(upload(pl, const_cast<int64_t**>(&pl->dp_ref.tmpl2_off), off1));
+            GTLS_TRY(upload(pl, const_cast<float2**>(&pl->dp_ref.tmpl2), t21));
+            GTLS_TRY(dev_alloc(pl, &pl->plist, pl->refine_k));
+            if (pl->tile_ok) {
+                bool fits1 = true;
+                for (int j = 0; j < dp.nd; ++j)
+                    if ((int64_t)(16 + h.dpts[j] + 2) + 32 > pl->tile_buf) fits1 = false;
+                const int64_t len1 = ((int64_t)pl->tile_buf - h.dmax - 3 - 96) & ~int64_t(63);
+                if (!fits1 || len1 < 64)
+                    return fail(GTLS_ERR_INVALID_ARG, "durations too long for the refinement tiles");
+                pl->tile_len_ref = (int)len1;
+                pl->tile_count_ref = (int)((n + len1 - 1) / len1);
+            }
+            const int topk_smem = ((dp.np + 31) / 32) * (int)sizeof(unsigned int);
+            if (topk_smem > 200 * 1024)
+                return fail(GTLS_ERR_INVALID_ARG, "too many periods for the refinement selection");
+            GTLS_CUDA(cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, topk_smem));
+        }
         GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
     }
     GTLS_CUDA(cudaFuncSetAttribute(k_fold_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1160,41 +1251,70 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     const int fold_smem = fold_smem_bytes(h.bucket_log2);
     const bool use_tiles = pl->tile_ok && !(flags & 4u);
     TileCfg tc{pl->tile_buf, pl->tile_len, pl->tile_count};
-    const int64_t max_win = n;  // stride >= 1
-    for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
-        const int cnt = std::min<int>(dk.chunk, dp.np - p0);
-        k_fold_sort<<<cnt, kFoldThreads, fold_smem, st>>>(dp, dc, dk, dq, p0);
+    GTLS_CUDA(cudaMemsetAsync(dq.refined, 0, (size_t)dp.np * sizeof(int32_t), st));
+
+    // fold + window search + per-period result for periods p0 .. p0+cnt-1,
+    // or for plist[0 .. cnt) when a list is given
+    auto chunk_pass = [&](const DevPlan& dpx, const TileCfg& tcx, int p0, int cnt,
+                          const int32_t* plist) -> gtls_status {
+        k_fold_sort<<<cnt, kFoldThreads, fold_smem, st>>>(dpx, dc, dk, dq, p0, plist);
         GTLS_CUDA(cudaGetLastError());
         GTLS_TRY(mark(pl, st, kStageFold, ev));
         if (use_tiles) {
             GTLS_CUDA(cudaMemsetAsync(pl->tile_counter, 0, sizeof(unsigned int), st));
             k_window_tiles<<<pl->n_sm, tiles::kThreads, pl->tile_buf * (int)sizeof(float), st>>>(
-                dp, dc, dk, dq, tc, p0, cnt, pl->tile_counter);
+                dpx, dc, dk, dq, tcx, p0, cnt, pl->tile_counter, plist);
         } else {
-            dim3 grid((unsigned)((max_win + kSearchThreads - 1) / kSearchThreads), (unsigned)h.max_kept,
+            dim3 grid((unsigned)((n + kSearchThreads - 1) / kSearchThreads), (unsigned)h.max_kept,
                       (unsigned)cnt);
-            k_window_search<<<grid, kSearchThreads, 0, st>>>(dp, dc, dk, dq, p0);
+            k_window_search<<<grid, kSearchThreads, 0, st>>>(dpx, dc, dk, dq, p0, plist);
         }
         GTLS_CUDA(cudaGetLastError());
         GTLS_TRY(mark(pl, st, kStageWindow, ev));
-        k_period_finalize<<<(cnt + 127) / 128, 128, 0, st>>>(dp, dc, dk, dq, p0, cnt);
+        k_period_finalize<<<(cnt + 127) / 128, 128, 0, st>>>(dpx, dc, dk, dq, p0, cnt, plist);
         GTLS_CUDA(cudaGetLastError());
         GTLS_TRY(mark(pl, st, kStageFinalize, ev));
         launches += 3;
         window_launches += 1;
-    }
-    k_sr_stats<<<1, 1024, 0, st>>>(dp.np, dq);
-    GTLS_CUDA(cudaGetLastError());
+        return GTLS_OK;
+    };
     const int hwin = h.median_window / 2;
     const int outs = std::min(1024, kMedianCap - 2 * hwin) & ~31;
     if (outs < 32) return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
-    k_median_sde<<<(dp.np + outs - 1) / outs, kMedianThreads,
-                   kMedianCap * (int)(sizeof(double) + sizeof(int)), st>>>(dp.np, hwin, outs, dq);
-    GTLS_CUDA(cudaGetLastError());
+    auto sr_sde = [&]() -> gtls_status {
+        k_sr_stats<<<1, 1024, 0, st>>>(dp.np, dq);
+        GTLS_CUDA(cudaGetLastError());
+        k_median_sde<<<(dp.np + outs - 1) / outs, kMedianThreads,
+                       kMedianCap * (int)(sizeof(double) + sizeof(int)), st>>>(dp.np, hwin, outs, dq);
+        GTLS_CUDA(cudaGetLastError());
+        launches += 2;
+        GTLS_TRY(mark(pl, st, kStageSrSde, ev));
+        return GTLS_OK;
+    };
+    for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
+        const int cnt = std::min<int>(dk.chunk, dp.np - p0);
+        GTLS_TRY(chunk_pass(dp, tc, p0, cnt, nullptr));
+    }
+    GTLS_TRY(sr_sde());
+    const int kref = pl->refine_k;
+    if (kref > 0) {
+        // two-stage T0 search (Sect. 2.5): the kref best periods by SDE(P)
+        // again with T0 step 1, then SR / SDE once more
+        k_topk<<<1, 1024, ((dp.np + 31) / 32) * sizeof(unsigned int), st>>>(dp.np, kref, dq, pl->plist);
+        GTLS_CUDA(cudaGetLastError());
+        launches += 1;
+        GTLS_TRY(mark(pl, st, kStageSrSde, ev));
+        TileCfg tc1{pl->tile_buf, pl->tile_len_ref, pl->tile_count_ref};
+        for (int r0 = 0; r0 < kref; r0 += dk.chunk) {
+            const int cnt = std::min<int>(dk.chunk, kref - r0);
+            GTLS_TRY(chunk_pass(pl->dp_ref, tc1, 0, cnt, pl->plist + r0));
+        }
+        GTLS_TRY(sr_sde());
+    }
+    GTLS_TRY(mark(pl, st, kStageSrSde, ev));
     k_best<<<1, 1024, 0, st>>>(dp, dc, dq);
     GTLS_CUDA(cudaGetLastError());
-    launches += 3;
-    GTLS_TRY(mark(pl, st, kStageSrSde, ev));
+    launches += 1;
     if (per) {
         const size_t np_ = (size_t)dp.np;
         if (per->chi2) GTLS_CUDA(cudaMemcpyAsync(per->chi2, dq.chi2, np_ * 8, cudaMemcpyDeviceToDevice, st));
@@ -1205,6 +1325,8 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
         if (per->sr) GTLS_CUDA(cudaMemcpyAsync(per->sr, dq.sr, np_ * 8, cudaMemcpyDeviceToDevice, st));
         if (per->sde_raw) GTLS_CUDA(cudaMemcpyAsync(per->sde_raw, dq.sde_raw, np_ * 8, cudaMemcpyDeviceToDevice, st));
         if (per->sde) GTLS_CUDA(cudaMemcpyAsync(per->sde, dq.sde, np_ * 8, cudaMemcpyDeviceToDevice, st));
+        if (per->refined)
+            GTLS_CUDA(cudaMemcpyAsync(per->refined, dq.refined, np_ * 4, cudaMemcpyDeviceToDevice, st));
     }
     unsigned int chk[4] = {0, 0, 0, 0};
     GTLS_CUDA(cudaMemcpyAsync(chk, dc.check, sizeof chk, cudaMemcpyDeviceToHost, st));
@@ -1214,6 +1336,7 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
         return fail(GTLS_ERR_INTERNAL, "device index check " + std::to_string(chk[0]) + " failed (value " +
                                            std::to_string(((long long)chk[3] << 32) | chk[1]) +
                                            ", limit " + std::to_string(chk[2]) + ")");
+    out->refined = kref;
     pl->profile.kernel_launches = launches;
     pl->profile.window_search_launches = window_launches;
     if (pl->profiling) GTLS_TRY(collect_profile(pl, ev));

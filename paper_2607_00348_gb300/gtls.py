@@ -44,7 +44,8 @@ class PlanParams(ctypes.Structure):
                 ("dur_ratio", ctypes.c_double), ("dt0", ctypes.c_double),
                 ("u1", ctypes.c_double), ("u2", ctypes.c_double),
                 ("median_window", ctypes.c_int32), ("periods_per_chunk", ctypes.c_int32),
-                ("periods_days", c_double_p), ("n_periods", ctypes.c_int64)]
+                ("periods_days", c_double_p), ("n_periods", ctypes.c_int64),
+                ("refine_periods", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -62,7 +63,7 @@ class Result(ctypes.Structure):
                 ("chi2_0", ctypes.c_double), ("period_idx", ctypes.c_int64),
                 ("dur_idx", ctypes.c_int32), ("dur_points", ctypes.c_int32),
                 ("t0_idx", ctypes.c_int64), ("uniform_dy", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("refined", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
@@ -83,7 +84,8 @@ class PeriodOutputs(ctypes.Structure):
     _fields_ = [("chi2", ctypes.c_void_p), ("dur_idx", ctypes.c_void_p),
                 ("t0_idx", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("t0", ctypes.c_void_p), ("sr", ctypes.c_void_p),
-                ("sde_raw", ctypes.c_void_p), ("sde", ctypes.c_void_p)]
+                ("sde_raw", ctypes.c_void_p), ("sde", ctypes.c_void_p),
+                ("refined", ctypes.c_void_p)]
 
 
 # (name, restype, argtypes) of every symbol declared in include/gtls.h
@@ -180,6 +182,7 @@ class PlanConfig:
     u2: float = 0.25
     median_window: int = 0
     periods_per_chunk: int = 0
+    refine_periods: int = 0
     periods_days: np.ndarray | None = None
 
 
@@ -192,7 +195,8 @@ class Plan:
         lib.gtls_plan_params_default(ctypes.byref(prm))
         for f in ("baseline_days", "n_points", "m_star", "r_star", "oversampling",
                   "period_min_days", "period_max_days", "k_min", "k_max", "q_cap",
-                  "dur_ratio", "dt0", "u1", "u2", "median_window", "periods_per_chunk"):
+                  "dur_ratio", "dt0", "u1", "u2", "median_window", "periods_per_chunk",
+                  "refine_periods"):
             v = getattr(cfg, f)
             setattr(prm, f, v if v is not None else 0)
         self._periods_in = None

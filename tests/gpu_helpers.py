@@ -16,7 +16,8 @@ def plan_for(lc_or_n, baseline, cfg=None, **kw):
                         dt0=cfg.get("dt0", 0.05), dur_ratio=cfg.get("dur_ratio", 1.1),
                         k_min=cfg.get("k_min", 20.05), k_max=cfg.get("k_max", 620.84),
                         q_cap=cfg.get("q_cap", 0.15), oversampling=cfg.get("oversampling", 3.0),
-                        periods_days=cfg.get("periods_days"))
+                        periods_days=cfg.get("periods_days"),
+                        refine_periods=cfg.get("refine_periods", 0))
     return pkg.Plan(pc)
 
 
@@ -45,7 +46,8 @@ def gpu_search(plan, t, y, dy):
                 t0=torch.empty(npd, dtype=torch.float64, device=dev),
                 sr=torch.empty(npd, dtype=torch.float64, device=dev),
                 sde_raw=torch.empty(npd, dtype=torch.float64, device=dev),
-                sde=torch.empty(npd, dtype=torch.float64, device=dev))
+                sde=torch.empty(npd, dtype=torch.float64, device=dev),
+                refined=torch.empty(npd, dtype=torch.int32, device=dev))
     res = plan.search(tt, yy, dd, per_period=outs)
     torch.cuda.synchronize()
     return res, {k: v.cpu().numpy() for k, v in outs.items()}

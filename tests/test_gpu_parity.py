@@ -217,3 +217,43 @@ def test_kepler_like_full_size_sampled_parity():
     assert abs(out["sde_raw"].mean()) < 1e-9
     assert out["sde_raw"].std() == pytest.approx(1.0, rel=1e-9)
     pl.close()
+
+
+def test_refinement_stage_matches_oracle():
+    # Sect. 2.5: the 200 best periods by SDE(P) re-searched with T0 step 1
+    lc = synth.short_white()
+    cfg = dict(lc.search, refine_periods=200)
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, lc.t, lc.y, lc.dy, refine_top_k=200)
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    assert res.refined == 200
+    assert np.array_equal(out["refined"].astype(bool), r_or.refined)
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out)
+    np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
+    assert res.period_idx == best_or["period_idx"]
+    assert (res.dur_idx, res.t0_idx) == (best_or["dur_idx"], best_or["t0_idx"])
+    assert res.t0 == best_or["t0"]
+    pl.close()
+
+
+def test_long_baseline_full_size_sampled_parity():
+    lc = synth.long_baseline()
+    cfg = lc.search
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    npd = op.periods.size
+    near = int(np.argmin(np.abs(op.periods - lc.injected["period"])))
+    sel = np.unique(np.concatenate([np.arange(0, npd, 20000), np.arange(near - 4, near + 5),
+                                    [npd - 1]]))
+    r_or = osr.search_periods(op, lc.t, lc.y, lc.dy, sel)
+    np.testing.assert_allclose(out["chi2"][sel], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out, sel)
+    assert abs(res.period - 123.4) / 123.4 < 2e-3
+    assert res.sde > 9.0
+    sr = out["sr"]
+    assert np.all(sr > 0) and np.all(sr <= 1.0)
+    assert abs(out["sde_raw"].mean()) < 1e-9
+    pl.close()

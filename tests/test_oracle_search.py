@@ -198,3 +198,29 @@ def test_median_window_reading():
     assert osr.median_window(3048) == 31
     assert osr.median_window(10) == 3
     assert osr.median_window(199_999) == 1999
+
+
+def test_refinement_never_raises_chi2_and_keeps_the_transit():
+    # Sect. 2.5: re-searching with T0 step 1 can only lower chi2(P) (its
+    # windows include the coarse ones), and the injected period stays best
+    lc = synth.short_white()
+    p = osr.plan(lc.n, lc.baseline_days, period_min_days=0.5, period_max_days=15.0)
+    r0, _, _, sde0, best0 = osr.full_search(p, lc.t, lc.y, lc.dy)
+    c0 = r0.chi2.copy()
+    r1, _, _, sde1, best1 = osr.full_search(p, lc.t, lc.y, lc.dy, refine_top_k=50)
+    assert r1.refined.sum() == 50
+    assert np.all(r1.chi2 <= c0 * (1 + 1e-12))
+    assert np.all(r1.chi2[~r1.refined] == c0[~r1.refined])
+    assert np.any(r1.chi2[r1.refined] < c0[r1.refined])
+    assert abs(best1["period"] - 3.7) / 3.7 < 0.01
+    assert r1.chi2[best1["period_idx"]] <= r0.chi2[best1["period_idx"]]
+    # the selection is the top of the coarse SDE
+    sel = np.flatnonzero(r1.refined)
+    assert np.array_equal(sel, osr.refine_selection(sde0, 50))
+    assert sde0[sel].min() >= np.delete(sde0, sel).max()
+
+
+def test_refinement_selection_ties_take_lower_index():
+    sde = np.array([1.0, 3.0, 3.0, 2.0, 3.0])
+    assert list(osr.refine_selection(sde, 2)) == [1, 2]
+    assert list(osr.refine_selection(sde, 4)) == [1, 2, 3, 4]
