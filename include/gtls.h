@@ -182,11 +182,84 @@ gtls_status gtls_search_host(gtls_plan* plan, const double* t, const double* y,
                              gtls_result* out);
 
 /*
- * Search n_lc light curves packed back to back (CSR): curve i is
- * t[offsets[i] .. offsets[i+1]) and likewise y, dy (device arrays);
- * offsets is a host array of n_lc + 1 entries; plans[i] must have been made
- * for curve i's n (plans may repeat).  out: host array of n_lc results.
- * Each result equals gtls_search on that curve alone.
+ * Batched search of many light curves (no counterpart in the paper, which
+ * searches one light curve at a time; its periods of different curves are
+ * as independent as those of one curve).  A batch references n_lc plans,
+ * one per curve (plans[i] made for curve i's n and baseline; a plan may
+ * appear once; the plans must outlive the batch and must not be searched on
+ * their own while the batch runs, since the batch writes their per-curve and
+ * per-period buffers).  The batch owns one chunk scratch shared by all
+ * curves (sized for the largest curve; `wave_slots` periods in flight, 0 =
+ * as many as fit 8 GiB, at most 4096) and runs the periods of all curves as
+ * waves of (curve, period range) segments through the same kernels as
+ * gtls_search.  Everything after the per-curve preparation is captured
+ * once into a CUDA graph and replayed by later searches (recaptured when
+ * the set of curves with uniform dy changes, or after gtls_batch_autotune).
+ * Results equal gtls_search on each curve alone.
+ * Errors: INVALID_ARG (n_lc outside [1, 65535], null or repeated plans,
+ * plans on another device), OOM, CUDA.
+ */
+typedef struct gtls_batch gtls_batch;
+
+typedef struct gtls_batch_info {
+    int64_t n_lc;
+    int64_t n_points;          /* all curves */
+    int64_t n_periods;         /* trial periods of all curves (coarse pass) */
+    double wpe;                /* window-point evaluations of all curves */
+    int32_t waves;             /* coarse waves of the captured graph (0 before the first search) */
+    int32_t wave_slots;        /* periods per wave */
+    int32_t tile_floats;       /* folded-curve floats staged per window-tile item */
+    int32_t graph_kernels;     /* kernels in the captured graph */
+    int64_t last_launches;     /* kernels launched by the last gtls_batch_search */
+    int64_t device_bytes;      /* device memory owned by the batch */
+    int32_t tuned;             /* 1 after gtls_batch_autotune */
+    int32_t reserved0;
+    double tuned_flops;        /* probe rate of the chosen configuration (2 x WPE / s) */
+} gtls_batch_info;
+
+gtls_status gtls_batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slots,
+                              gtls_batch** out);
+
+/*
+ * Search every curve of the batch: curve i is t[offsets[i] .. offsets[i+1])
+ * and likewise y, dy (device arrays, caller-owned, read only);
+ * offsets: host array of n_lc + 1 entries whose differences equal the
+ * plans' n_points.  out: host array of n_lc results.  One stream
+ * synchronisation after the preparation (input validation) and one at the
+ * end.  Errors: INVALID_ARG (sizes, NaN/inf, dy <= 0; the message names the
+ * curve), INTERNAL (a device index check), CUDA.
+ */
+gtls_status gtls_batch_search(gtls_batch* batch, const double* t, const double* y, const double* dy,
+                              const int64_t* offsets, void* stream, gtls_result* out);
+
+/*
+ * Choose the wave size (the largest, a half, a quarter) and the staged tile
+ * size (the plans' own, 40960, 32768 floats) by timing the coarse pass of
+ * a probe (four runs of 256 periods spread over each of the first four
+ * curves that take the tiled kernel) on these inputs; keeps the fastest.
+ * Results do not depend on the choice.  Same arguments as
+ * gtls_batch_search.
+ */
+gtls_status gtls_batch_autotune(gtls_batch* batch, const double* t, const double* y, const double* dy,
+                                const int64_t* offsets, void* stream);
+
+gtls_status gtls_batch_get_info(const gtls_batch* batch, gtls_batch_info* out);
+
+/*
+ * Per-period outputs of curve lc (0 <= lc < n_lc) from the last
+ * gtls_batch_search: device arrays of that curve's n_periods, as in
+ * gtls_search (null members are skipped).  Enqueued on `stream`.
+ */
+gtls_status gtls_batch_get_period_outputs(const gtls_batch* batch, int64_t lc,
+                                          const gtls_period_outputs* per, void* stream);
+
+/* Release the batch's device memory and graph (NULL is a no-op). */
+void gtls_batch_destroy(gtls_batch* batch);
+
+/*
+ * One-call batched search: gtls_batch_create (default wave size),
+ * gtls_batch_search, gtls_batch_destroy.  Same arguments and results as
+ * gtls_batch_search with the plans given directly (each plan once).
  */
 gtls_status gtls_search_batch(gtls_plan* const* plans, int64_t n_lc,
                               const double* t, const double* y, const double* dy,

@@ -5,6 +5,8 @@ The search itself lives in ``csrc/`` (CUDA for sm_103a behind the C ABI of
 """
 
 from .gtls import (  # noqa: F401
+    Batch,
+    BatchInfo,
     GtlsError,
     Plan,
     PlanConfig,

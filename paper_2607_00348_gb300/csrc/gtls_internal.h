@@ -42,6 +42,8 @@ struct DevPlan {
     const int32_t* cfg_nc;      // phase-column lanes per window block per duration
     const int64_t* tmpl2_off;   // offset of duration j in tmpl2 (float2 units)
     const float2* tmpl2;        // template pairs (s_k, s_{k+nc}) of column-pair durations
+    int32_t median_half;        // half width h of the running-median window
+    int32_t refine_k;           // periods re-searched with T0 step 1 (0: none)
 };
 
 // Per-light-curve derived arrays (n long unless noted).
@@ -86,7 +88,41 @@ struct DevPeriod {
     double* stats;            // [0] chi2_min [1] mean SR [2] std SR
     unsigned int* check;      // same words as DevCurve::check
     int32_t* refined;         // 1 where the period was re-searched with T0 step 1
+    int32_t* plist;           // the refine_k periods to re-search, in rank order
     gtls_result* result;      // device copy of the best candidate
+};
+
+// Tile shape of one light curve in the tiled window kernel.
+struct DevTiles {
+    int32_t len;              // window starts per tile (L)
+    int32_t count;            // tiles per period
+};
+
+// Per-light-curve descriptors of a search (device arrays, one entry per
+// curve; a single search uses one entry).
+struct DevSet {
+    const DevPlan* plans;
+    const DevCurve* curves;
+    const DevPeriod* outs;
+    const DevTiles* tiles;
+};
+
+// Which (light curve, period) each slot of a wave holds: a wave is up to
+// kMaxSeg segments of consecutive periods (or consecutive positions of the
+// curve's refinement list), passed by value.
+constexpr int kMaxSeg = 32;
+struct WaveSeg {
+    int32_t lc;               // light curve
+    int32_t first;            // first period (or refinement-list position)
+    int32_t slot0;            // first slot of the segment in the wave
+    int32_t item0;            // first window-tile item of the segment
+};
+struct SlotMap {
+    int32_t nseg;
+    int32_t slots;            // slots in the wave
+    int32_t items;            // window-tile items in the wave
+    int32_t from_list;        // periods are refinement-list positions
+    WaveSeg seg[kMaxSeg];
 };
 
 }  // namespace gtls
@@ -113,7 +149,10 @@ struct gtls_plan {
     int refine_k = 0;
     gtls::DevPlan dp_ref{};
     int tile_len_ref = 0, tile_count_ref = 0;
-    int32_t* plist = nullptr;
+    // one-entry device descriptor sets of the coarse and refinement passes
+    gtls::DevSet set{}, set_ref{};
+    int64_t* prep_off = nullptr;        // device {0, n}: the curve's offsets
+    bool chunk_ready = false;           // dk allocated (first single search)
     std::vector<float> tmpl_pad;        // host copy of the zero-padded template table
     std::vector<int64_t> tmpl_pad_off;
     // stage profiling: events recorded on the search stream when enabled

@@ -147,6 +147,25 @@ __device__ long long block_exclusive_scan(long long v, long long* warp_sums, lon
     return out;
 }
 
+// Light curve and period held by `slot` of a wave (segments ascend in
+// slot0); false when the period index is out of range.
+__device__ __forceinline__ bool resolve_slot(const DevSet& ds, const SlotMap& sm, int slot, int& lc, int& p)
+{
+    int s = 0;
+    while (s + 1 < sm.nseg && sm.seg[s + 1].slot0 <= slot) ++s;
+    lc = sm.seg[s].lc;
+    const int q = sm.seg[s].first + (slot - sm.seg[s].slot0);
+    p = sm.from_list ? ds.outs[lc].plist[q] : q;
+    return p >= 0 && p < ds.plans[lc].np;
+}
+
+// Work size of the per-curve preparation kernels for n points.
+__host__ __device__ __forceinline__ int prep_blocks_for(int64_t n)
+{
+    const int64_t b = (n + 255) / 256;
+    return (int)(b < 1024 ? b : 1024);
+}
+
 }  // namespace
 
 #include "window_tiles.cuh"
@@ -157,14 +176,33 @@ namespace {
 // per-curve preparation
 // ---------------------------------------------------------------------------
 
-__global__ void k_curve_minmax(const double* __restrict__ t, const double* __restrict__ y,
-                               const double* __restrict__ dy, int64_t n, DevCurve dc)
+// Reset of the per-curve reduction words (block lc0 + b: curve lc0 + b).
+__global__ void k_curve_reset(DevSet ds, int lc0)
 {
+    const DevCurve& dc = ds.curves[lc0 + blockIdx.x];
+    if (threadIdx.x == 0) *dc.tmin_key = ~0ull;
+    if (threadIdx.x == 1) *dc.flags = 0u;
+    if (threadIdx.x >= 2 && threadIdx.x < 6) dc.check[threadIdx.x - 2] = 0u;
+}
+
+// Curve lc = lc0 + blockIdx.y holds points off[lc] .. off[lc+1] of t, y, dy;
+// its blocks are the first prep_blocks_for(n) of the row.
+__global__ void k_curve_minmax(const double* __restrict__ t, const double* __restrict__ y,
+                               const double* __restrict__ dy, const int64_t* __restrict__ off,
+                               DevSet ds, int lc0)
+{
+    const int lc = lc0 + blockIdx.y;
+    const int64_t o = off[lc], n = off[lc + 1] - o;
+    const int nb = prep_blocks_for(n);
+    if ((int)blockIdx.x >= nb || n <= 0) return;
+    t += o;
+    y += o;
+    dy += o;
+    const DevCurve& dc = ds.curves[lc];
     unsigned long long kmin = ~0ull;
     unsigned int fl = 0;
     const double dy0 = dy[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)nb * blockDim.x) {
         const double ti = t[i], yi = y[i], di = dy[i];
         if (!isfinite(ti) || !isfinite(yi) || !isfinite(di)) fl |= 1u;
         if (!(di > 0.0)) fl |= 2u;
@@ -173,10 +211,10 @@ __global__ void k_curve_minmax(const double* __restrict__ t, const double* __res
         kmin = k < kmin ? k : kmin;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kmin, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kmin, o2);
         kmin = k2 < kmin ? k2 : kmin;
-        fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        fl |= __shfl_xor_sync(0xffffffffu, fl, o2);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMin(dc.tmin_key, kmin);
@@ -185,14 +223,23 @@ __global__ void k_curve_minmax(const double* __restrict__ t, const double* __res
 }
 
 __global__ void k_curve_prep(const double* __restrict__ t, const double* __restrict__ y,
-                             const double* __restrict__ dy, int64_t n, int e, DevCurve dc)
+                             const double* __restrict__ dy, const int64_t* __restrict__ off,
+                             DevSet ds, int lc0)
 {
     __shared__ double red[32];
+    const int lc = lc0 + blockIdx.y;
+    const int64_t o = off[lc], n = off[lc + 1] - o;
+    const int nb = prep_blocks_for(n);
+    if ((int)blockIdx.x >= nb || n <= 0) return;
+    t += o;
+    y += o;
+    dy += o;
+    const DevCurve dc = ds.curves[lc];
+    const int e = ds.plans[lc].time_exponent;
     const double t_ref = double_from_order_key(*dc.tmin_key);
     const double scale = ldexp(1.0, e);
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)nb * blockDim.x) {
         const double dt = t[i] - t_ref;
         const double r = 1.0 - y[i];
         const double w = 1.0 / (dy[i] * dy[i]);
@@ -204,7 +251,7 @@ __global__ void k_curve_prep(const double* __restrict__ t, const double* __restr
         acc += w * r * r;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -214,14 +261,24 @@ __global__ void k_curve_prep(const double* __restrict__ t, const double* __restr
     }
 }
 
-__global__ void k_curve_reduce(int nparts, const double* __restrict__ dy, DevCurve dc)
+// One thread per curve (lc0 + global thread index < lc_end): chi2_0 from
+// the block partials in block order, t_ref, the uniform weight; the
+// validity flags go to flags_out[lc].
+__global__ void k_curve_reduce(const double* __restrict__ dy, const int64_t* __restrict__ off, DevSet ds,
+                               int lc0, int lc_end, unsigned int* flags_out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int lc = lc0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (lc >= lc_end) return;
+    const int64_t o = off[lc], n = off[lc + 1] - o;
+    const DevCurve dc = ds.curves[lc];
+    const int nparts = prep_blocks_for(n);
     double s = 0.0;
     for (int i = 0; i < nparts; ++i) s += dc.part[i];
+    const unsigned int fl = *dc.flags;
     dc.scal[0] = double_from_order_key(*dc.tmin_key);
     dc.scal[1] = s;
-    dc.scal[2] = (*dc.flags & 4u) ? 0.0 : 1.0 / (dy[0] * dy[0]);
+    dc.scal[2] = (fl & 4u) ? 0.0 : 1.0 / (dy[o] * dy[o]);
+    flags_out[lc] = fl;
 }
 
 // ---------------------------------------------------------------------------
@@ -229,18 +286,20 @@ __global__ void k_curve_reduce(int nparts, const double* __restrict__ dy, DevCur
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kFoldThreads)
-k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, const int32_t* plist)
+k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
 {
     extern __shared__ unsigned char smem[];
+    const int slot_id = blockIdx.x;
+    int lc, p;
+    if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
+    const DevPlan& dp = ds.plans[lc];
+    const DevCurve dc = ds.curves[lc];
     const int nb = 1 << dp.bucket_log2;
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
     uint32_t* start = hist + nb;
     long long* warp_sums = reinterpret_cast<long long*>(start + nb);
     long long* total = warp_sums + 32;
 
-    const int slot_id = blockIdx.x;
-    const int p = plist ? plist[slot_id] : p0 + slot_id;
-    if (p >= dp.np) return;
     const int64_t n = dp.n;
     const long long P = dp.p_lat[p];
     const float inv_p = dp.inv_p[p];
@@ -257,7 +316,7 @@ k_fold_sort(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, const in
     long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
     const bool uniform = dc.scal[2] > 0.0;
 
-    if (threadIdx.x == 0) dq.best[p] = ~0ull;
+    if (threadIdx.x == 0) ds.outs[lc].best[p] = ~0ull;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
 
@@ -363,12 +422,14 @@ __device__ __forceinline__ int kept_j(const DevPlan& dp, int p, int slot)
 }
 
 __global__ void __launch_bounds__(kSearchThreads)
-k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, const int32_t* plist)
+k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
 {
     __shared__ unsigned long long red[kSearchThreads / 32];
     const int slot_id = blockIdx.z;
-    const int p = plist ? plist[slot_id] : p0 + slot_id;
-    if (p >= dp.np) return;
+    int lc, p;
+    if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
+    const DevPlan& dp = ds.plans[lc];
+    const DevCurve dc = ds.curves[lc];
     const int j = kept_j(dp, p, blockIdx.y);
     if (j < 0) return;
     const int d = dp.dpts[j], st = dp.stride[j];
@@ -417,7 +478,7 @@ k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, cons
     if (threadIdx.x == 0) {
         unsigned long long b = red[0];
         for (int w = 1; w < kSearchThreads / 32; ++w) b = red[w] < b ? red[w] : b;
-        atomicMin(&dq.best[p], b);
+        atomicMin(&ds.outs[lc].best[p], b);
     }
 }
 
@@ -425,41 +486,56 @@ k_window_search(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, cons
 // tiled window search (uniform weights): see window_tiles.cuh
 // ---------------------------------------------------------------------------
 
-struct TileCfg {
-    int buf;     // floats of folded curve staged per item
-    int len;     // window starts per tile (L)
-    int tiles;   // tiles per period
-};
-
 __global__ void __launch_bounds__(tiles::kThreads, 1)
-k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, int p0, int cnt,
-               unsigned int* counter, const int32_t* plist)
+k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int buf, unsigned int* counter)
 {
     using namespace tiles;
     extern __shared__ float tile_smem[];
     __shared__ DurTask dur[kMaxDur];
-    __shared__ int s_item, s_ndur, s_total, s_task;
+    __shared__ int s_item, s_ndur, s_total, s_task, s_lc, s_p, s_slot, s_x0, s_len;
     __shared__ unsigned long long s_best[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int items = cnt * tc.tiles;
-    const float w_uni = (float)dc.scal[2];
-    const int64_t n = dp.n;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(counter, 1u);
+            s_item = item;
+            if (item < sm.items) {
+                int g = 0;
+                while (g + 1 < sm.nseg && sm.seg[g + 1].item0 <= item) ++g;
+                const int lcg = sm.seg[g].lc;
+                const DevTiles tl = ds.tiles[lcg];
+                const int rel = item - sm.seg[g].item0;
+                const int k = rel / tl.count, tau = rel - k * tl.count;
+                const int q = sm.seg[g].first + k;
+                int pp = sm.from_list ? ds.outs[lcg].plist[q] : q;
+                if (!in_range(ds.curves[lcg].check, 22, pp, ds.plans[lcg].np)) pp = -1;
+                s_lc = lcg;
+                s_p = pp;
+                s_slot = sm.seg[g].slot0 + k;
+                s_x0 = tau * tl.len;
+                s_len = tl.len;
+            }
+        }
         __syncthreads();
         const int item = s_item;
-        if (item >= items) break;
-        const int slot = item / tc.tiles, tau = item - (item / tc.tiles) * tc.tiles;
-        const int p = plist ? plist[slot] : p0 + slot;
-        const int x0 = tau * tc.len;
+        if (item >= sm.items) break;
+        const int lc = s_lc, p = s_p, slot = s_slot, x0 = s_x0, tile_len = s_len;
+        if (p < 0) {   // block-uniform: a failed check skips the item
+            __syncthreads();
+            continue;
+        }
+        const DevPlan& dp = ds.plans[lc];
+        unsigned int* const check = ds.curves[lc].check;
+        const float w_uni = (float)ds.curves[lc].scal[2];
+        const int64_t n = dp.n;
 
         // stage the folded, padded curve [x0, x0 + buf) (zeros past its end)
         const float* src = dk.rs + (int64_t)slot * dk.pad_stride + x0;
-        const int valid = (int)min((int64_t)tc.buf, n + (int64_t)dp.dmax_p[p] + kPadMargin - x0);
+        const int valid = (int)min((int64_t)buf, n + (int64_t)dp.dmax_p[p] + kPadMargin - x0);
         const int v4 = valid >> 2;
         for (int i = threadIdx.x; i < v4; i += blockDim.x)
             reinterpret_cast<float4*>(tile_smem)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
-        for (int i = (v4 << 2) + threadIdx.x; i < tc.buf; i += blockDim.x)
+        for (int i = (v4 << 2) + threadIdx.x; i < buf; i += blockDim.x)
             tile_smem[i] = i < valid ? src[i] : 0.0f;
 
         // durations of the period, longest first, with their task ranges
@@ -472,14 +548,14 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
                 const bool kept = j >= lo && (j == lo || dp.dpts[j] != dp.dpts[j - 1]);
                 const unsigned int mask = __ballot_sync(0xffffffffu, kept);
                 const int k = kcount + __popc(mask & ((1u << lane) - 1u));
-                if (kept && in_range(dc.check, 19, k, kMaxDur)) {
+                if (kept && in_range(check, 19, k, kMaxDur)) {
                     DurTask t;
                     t.j = j;
                     t.d = dp.dpts[j];
                     t.st = dp.stride[j];
                     t.m_total = (int)((n + t.st - 1) / t.st);
                     t.m_a = (x0 + t.st - 1) / t.st;
-                    t.m_b = min(t.m_total, (x0 + tc.len + t.st - 1) / t.st);
+                    t.m_b = min(t.m_total, (x0 + tile_len + t.st - 1) / t.st);
                     const int nwin = max(0, t.m_b - t.m_a);
                     t.variant = dp.cfg_variant[j];
                     t.nc = dp.cfg_nc[j];
@@ -488,15 +564,15 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
                     t.tasks = (nwin + t.per_task - 1) / t.per_task;
                     const int jrows = (t.d + t.st - 1) / t.st;
                     t.jrows = jrows;
-                    t.toff = dp.tmpl_off[j];
-                    t.t2off = dp.tmpl2_off[j];
+                    t.tg = dp.tmpl + dp.tmpl_off[j];
+                    t.tg2 = dp.tmpl2 + dp.tmpl2_off[j];
                     t.inv_sum_t = dp.inv_sum_t[j] * (1.0f / 1099511627776.0f);  // 2^-40 fixed point
                     t.inv_sum_t_f = dp.inv_sum_t[j];
                     t.sum_t2 = dp.sum_t2[j];
                     // rows up to m + w + jrows - 1 and columns up to st + 31 must stay in the buffer
-                    const int m_max_start = (x0 + tc.buf - 32) / t.st - t.w - jrows;
+                    const int m_max_start = (x0 + buf - 32) / t.st - t.w - jrows;
                     t.hi_start = min(t.m_total - t.w, m_max_start);
-                    if (t.tasks > 0) in_range(dc.check, 20, (int64_t)t.m_a, (int64_t)m_max_start + 1);
+                    if (t.tasks > 0) in_range(check, 20, (int64_t)t.m_a, (int64_t)m_max_start + 1);
                     t.first = 0;
                     dur[k] = t;
                 }
@@ -548,13 +624,13 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
             c.nc = t.nc;
             c.lg_nc = __ffs(t.nc) - 1;
             c.jrows = t.jrows;
-            c.tg2 = dp.tmpl2 + t.t2off;
+            c.tg2 = t.tg2;
             c.m_first = t.m_a + (task - t.first) * t.per_task;
             c.m_a = t.m_a;
             c.m_b = t.m_b;
             c.hi_start = t.hi_start;
             c.m_total = t.m_total;
-            c.tg = dp.tmpl + t.toff;
+            c.tg = t.tg;
             c.inv_sum_t = t.inv_sum_t;
             c.inv_sum_t_f = t.inv_sum_t_f;
             c.sum_t2 = t.sum_t2;
@@ -579,7 +655,7 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
         if (threadIdx.x == 0) {
             unsigned long long b = s_best[0];
             for (int w = 1; w < kWarps; ++w) b = s_best[w] < b ? s_best[w] : b;
-            atomicMin(&dq.best[p], b);
+            atomicMin(&ds.outs[lc].best[p], b);
         }
     }
 }
@@ -588,13 +664,15 @@ k_window_tiles(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, TileCfg tc, i
 // per-period result: chi2(P), depth, T0 of the minimum
 // ---------------------------------------------------------------------------
 
-__global__ void k_period_finalize(DevPlan dp, DevCurve dc, DevChunk dk, DevPeriod dq, int p0, int cnt,
-                                  const int32_t* plist)
+__global__ void k_period_finalize(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
 {
     const int slot_id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot_id >= cnt) return;
-    const int p = plist ? plist[slot_id] : p0 + slot_id;
-    if (p >= dp.np) return;
+    if (slot_id >= sm.slots) return;
+    int lc, p;
+    if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
+    const DevPlan& dp = ds.plans[lc];
+    const DevCurve dc = ds.curves[lc];
+    const DevPeriod dq = ds.outs[lc];
     const unsigned long long b = dq.best[p];
     const float dchi = float_from_order_key((unsigned int)(b >> 32));
     const int j = (int)((b >> 24) & 0xffull);
@@ -636,9 +714,8 @@ __device__ double block_sum_fixed(double v, double* sh)
     return r;
 }
 
-__global__ void __launch_bounds__(1024) k_sr_stats(int np, DevPeriod dq)
+__device__ void sr_stats_body(int np, const DevPeriod& dq, double* sh)
 {
-    __shared__ double sh[1024];
     double mn = INFINITY;
     for (int i = threadIdx.x; i < np; i += blockDim.x) mn = fmin(mn, dq.chi2[i]);
     sh[threadIdx.x] = mn;
@@ -673,15 +750,29 @@ __global__ void __launch_bounds__(1024) k_sr_stats(int np, DevPeriod dq)
     }
 }
 
+__global__ void __launch_bounds__(1024) k_sr_stats(int np, DevPeriod dq)
+{
+    __shared__ double sh[1024];
+    sr_stats_body(np, dq, sh);
+}
+
+// One block per curve lc0 + blockIdx.x.
+__global__ void __launch_bounds__(1024) k_sr_stats_set(DevSet ds, int lc0)
+{
+    __shared__ double sh[1024];
+    const int lc = lc0 + blockIdx.x;
+    const DevPeriod dq = ds.outs[lc];
+    sr_stats_body(ds.plans[lc].np, dq, sh);
+}
+
 // Lower running median of sde_raw over [i-h, i+h] (truncated), one block per
 // `outs` consecutive outputs: the block sorts the union of its windows once
 // (bitonic, by value then position) and every thread walks the sorted list.
-__global__ void __launch_bounds__(kMedianThreads) k_median_sde(int np, int h, int outs, DevPeriod dq)
+__device__ void median_body(int np, int h, int outs, int blk, const DevPeriod& dq, unsigned char* smem)
 {
-    extern __shared__ unsigned char smem[];
     double* val = reinterpret_cast<double*>(smem);
     int* pos = reinterpret_cast<int*>(val + kMedianCap);
-    const int i0 = blockIdx.x * outs;
+    const int i0 = blk * outs;
     const int lo = max(0, i0 - h);
     const int hi = min(np - 1, i0 + outs - 1 + h);
     const int len = hi - lo + 1;
@@ -742,14 +833,46 @@ __global__ void __launch_bounds__(kMedianThreads) k_median_sde(int np, int h, in
     }
 }
 
-// The k periods with the largest SDE (ties: lower index first), in rank
-// order, into plist; flags them in dq.refined.  One block, k argmax passes
-// over the periods not yet taken (a bit mask in shared memory).
-__global__ void __launch_bounds__(1024) k_topk(int np, int k, DevPeriod dq, int32_t* plist)
+__global__ void __launch_bounds__(kMedianThreads) k_median_sde(int np, int h, int outs, DevPeriod dq)
+{
+    extern __shared__ unsigned char smem[];
+    median_body(np, h, outs, blockIdx.x, dq, smem);
+}
+
+// Outputs per block of the running median for half width h.
+__host__ __device__ __forceinline__ int median_outs(int h)
+{
+    const int o = kMedianCap - 2 * h;
+    return (o < 1024 ? o : 1024) & ~31;
+}
+
+// Row blockIdx.y: curve lc0 + blockIdx.y; its blocks are the first
+// ceil(np / median_outs(h)) of the row.
+__global__ void __launch_bounds__(kMedianThreads) k_median_sde_set(DevSet ds, int lc0)
+{
+    extern __shared__ unsigned char smem[];
+    const int lc = lc0 + blockIdx.y;
+    const int np = ds.plans[lc].np, h = ds.plans[lc].median_half;
+    const int outs = median_outs(h);
+    if (outs < 32 || (int)blockIdx.x * outs >= np) return;
+    const DevPeriod dq = ds.outs[lc];
+    median_body(np, h, outs, blockIdx.x, dq, smem);
+}
+
+// Curve lc0 + blockIdx.x: clears its refined flags, then takes the
+// refine_k periods with the largest SDE (ties: lower index first), in rank
+// order, into its plist and flags them.  k argmax passes over the periods
+// not yet taken (a bit mask in shared memory).
+__global__ void __launch_bounds__(1024) k_topk(DevSet ds, int lc0)
 {
     extern __shared__ unsigned int taken[];
     __shared__ double bv[1024];
     __shared__ int bi[1024];
+    const int lc = lc0 + blockIdx.x;
+    const int np = ds.plans[lc].np, k = ds.plans[lc].refine_k;
+    const DevPeriod dq = ds.outs[lc];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) dq.refined[i] = 0;
+    if (k <= 0) return;
     const int words = (np + 31) >> 5;
     for (int w = threadIdx.x; w < words; w += blockDim.x) taken[w] = 0u;
     __syncthreads();
@@ -781,21 +904,27 @@ __global__ void __launch_bounds__(1024) k_topk(int np, int k, DevPeriod dq, int3
         if (threadIdx.x == 0) {
             const int b = bi[0];
             if (in_range(dq.check, 21, b, np)) {
-                plist[r] = b;
+                dq.plist[r] = b;
                 taken[b >> 5] |= 1u << (b & 31);
                 dq.refined[b] = 1;
             } else {
-                plist[r] = 0;
+                dq.plist[r] = 0;
             }
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPeriod dq)
+// Curve lc0 + blockIdx.x: the candidate of largest SDE into its result
+// (and results[lc], checks[4 lc ..] when given).
+__global__ void __launch_bounds__(1024) k_best(DevSet ds, int lc0, gtls_result* results, unsigned int* checks)
 {
     __shared__ double bv[1024];
     __shared__ int bi[1024];
+    const int lc = lc0 + blockIdx.x;
+    const DevPlan& dp = ds.plans[lc];
+    const DevCurve dc = ds.curves[lc];
+    const DevPeriod dq = ds.outs[lc];
     double v = -INFINITY;
     int idx = 0x7fffffff;
     for (int i = threadIdx.x; i < dp.np; i += blockDim.x) {
@@ -821,10 +950,13 @@ __global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPerio
     }
     if (threadIdx.x == 0) {
         const int b = bi[0];
-        if (!in_range(dc.check, 17, b, dp.np)) return;
-        gtls_result r;
-        const int j = dq.dur[b];
-        if (!in_range(dc.check, 18, j, dp.nd)) return;
+        gtls_result r{};
+        const int j = in_range(dc.check, 17, b, dp.np) ? dq.dur[b] : -1;
+        if (j < 0 || !in_range(dc.check, 18, j, dp.nd)) {
+            if (checks)
+                for (int u = 0; u < 4; ++u) checks[4 * lc + u] = dc.check[u];
+            return;
+        }
         r.period = dp.periods[b];
         r.duration_days = dp.q[j] * dp.periods[b];
         r.t0 = dq.t0[b];
@@ -838,8 +970,11 @@ __global__ void __launch_bounds__(1024) k_best(DevPlan dp, DevCurve dc, DevPerio
         r.dur_points = dp.dpts[j];
         r.t0_idx = dq.t0i[b];
         r.uniform_dy = dc.scal[2] > 0.0 ? 1 : 0;
-        r.refined = 0;
+        r.refined = dp.refine_k;
         *dq.result = r;
+        if (results) results[lc] = r;
+        if (checks)
+            for (int u = 0; u < 4; ++u) checks[4 * lc + u] = dc.check[u];
     }
 }
 
@@ -943,6 +1078,39 @@ int fold_smem_bytes(int bucket_log2)
     return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long);
 }
 
+int topk_smem_bytes(int np, int k)
+{
+    return k > 0 ? ((np + 31) / 32) * (int)sizeof(unsigned int) : 0;
+}
+
+constexpr int kMedianSmem = kMedianCap * (int)(sizeof(double) + sizeof(int));
+
+// Every kernel with dynamic shared memory may use up to the device's opt-in
+// limit (set once per device, so that plans of any size coexist).
+gtls_status configure_kernels(int dev)
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return GTLS_OK;
+    int optin = 0;
+    GTLS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto allow = [&](const void* fn) -> gtls_status {
+        cudaFuncAttributes a{};
+        GTLS_CUDA(cudaFuncGetAttributes(&a, fn));
+        GTLS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       optin - (int)a.sharedSizeBytes));
+        return GTLS_OK;
+    };
+    GTLS_TRY(allow((const void*)k_fold_sort));
+    GTLS_TRY(allow((const void*)k_window_tiles));
+    GTLS_TRY(allow((const void*)k_median_sde));
+    GTLS_TRY(allow((const void*)k_median_sde_set));
+    GTLS_TRY(allow((const void*)k_topk));
+    done.push_back(dev);
+    return GTLS_OK;
+}
+
 gtls_status create_device(gtls_plan* pl)
 {
     const PlanHost& h = pl->host;
@@ -955,6 +1123,11 @@ gtls_status create_device(gtls_plan* pl)
     dp.idx_bits = h.idx_bits;
     dp.bucket_log2 = h.bucket_log2;
     dp.max_kept = h.max_kept;
+    dp.median_half = h.median_window / 2;
+    if (median_outs(dp.median_half) < 32)
+        return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
+    dp.refine_k = std::min<int>(h.prm.refine_periods, dp.np);
+    GTLS_TRY(configure_kernels(pl->device));
     std::vector<float> inv_sum_t(dp.nd), sum_t2f(dp.nd);
     for (int j = 0; j < dp.nd; ++j) {
         inv_sum_t[j] = (float)(1.0 / h.sum_t[j]);
@@ -1017,14 +1190,7 @@ gtls_status create_device(gtls_plan* pl)
     chunk = std::min<int64_t>(chunk, 1024);
     if (h.prm.periods_per_chunk > 0) chunk = h.prm.periods_per_chunk;
     chunk = std::min<int64_t>(chunk, dp.np);
-    dk.chunk = (int32_t)chunk;
-    GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.fold_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.slot, chunk * dk.fold_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.sidx, chunk * dk.fold_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.rs, chunk * dk.pad_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.ws, chunk * dk.pad_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.wrs, chunk * dk.pad_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.pf, chunk * dk.pad_stride));
+    dk.chunk = (int32_t)chunk;   // allocated by the first single-curve search
 
     DevPeriod& dq = pl->dq;
     const int64_t np_ = dp.np;
@@ -1083,8 +1249,6 @@ gtls_status create_device(gtls_plan* pl)
             pl->tile_buf = buf;
             pl->tile_len = (int)len;
             pl->tile_count = (int)((n + len - 1) / len);
-            GTLS_CUDA(cudaFuncSetAttribute(k_window_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           buf * (int)sizeof(float)));
             int64_t pos2 = 0;
             for (int j = 0; j < dp.nd; ++j) {
                 const int st = h.stride[j];
@@ -1126,7 +1290,7 @@ gtls_status create_device(gtls_plan* pl)
 
         // refinement stage: every duration with T0 step 1 through the (C1, S)
         // variant (one column per lane)
-        pl->refine_k = std::min<int>(h.prm.refine_periods, dp.np);
+        pl->refine_k = dp.refine_k;
         GTLS_TRY(dev_alloc(pl, &pl->dq.refined, dp.np));
         if (pl->refine_k > 0) {
             pl->dp_ref = dp;
@@ -1147,7 +1311,7 @@ gtls_status create_device(gtls_plan* pl)
             GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_nc), ones));
             GTLS_TRY(upload(pl, const_cast<int64_t**>(&pl->dp_ref.tmpl2_off), off1));
             GTLS_TRY(upload(pl, const_cast<float2**>(&pl->dp_ref.tmpl2), t21));
-            GTLS_TRY(dev_alloc(pl, &pl->plist, pl->refine_k));
+            GTLS_TRY(dev_alloc(pl, &pl->dq.plist, pl->refine_k));
             if (pl->tile_ok) {
                 bool fits1 = true;
                 for (int j = 0; j < dp.nd; ++j)
@@ -1158,17 +1322,44 @@ gtls_status create_device(gtls_plan* pl)
                 pl->tile_len_ref = (int)len1;
                 pl->tile_count_ref = (int)((n + len1 - 1) / len1);
             }
-            const int topk_smem = ((dp.np + 31) / 32) * (int)sizeof(unsigned int);
-            if (topk_smem > 200 * 1024)
+            if (topk_smem_bytes(dp.np, pl->refine_k) > 200 * 1024)
                 return fail(GTLS_ERR_INVALID_ARG, "too many periods for the refinement selection");
-            GTLS_CUDA(cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, topk_smem));
         }
         GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
     }
-    GTLS_CUDA(cudaFuncSetAttribute(k_fold_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   fold_smem_bytes(h.bucket_log2)));
-    GTLS_CUDA(cudaFuncSetAttribute(k_median_sde, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kMedianCap * (int)(sizeof(double) + sizeof(int))));
+
+    // one-entry descriptor sets of this plan's own searches
+    {
+        DevPlan* d_plans = nullptr;
+        DevCurve* d_curves = nullptr;
+        DevPeriod* d_outs = nullptr;
+        DevTiles* d_tiles = nullptr;
+        GTLS_TRY(upload(pl, &d_plans, std::vector<DevPlan>{dp, pl->refine_k > 0 ? pl->dp_ref : dp}));
+        GTLS_TRY(upload(pl, &d_curves, std::vector<DevCurve>{dc}));
+        GTLS_TRY(upload(pl, &d_outs, std::vector<DevPeriod>{pl->dq}));
+        GTLS_TRY(upload(pl, &d_tiles, std::vector<DevTiles>{DevTiles{pl->tile_len, pl->tile_count},
+                                                             DevTiles{pl->tile_len_ref, pl->tile_count_ref}}));
+        pl->set = DevSet{d_plans, d_curves, d_outs, d_tiles};
+        pl->set_ref = DevSet{d_plans + 1, d_curves, d_outs, d_tiles + 1};
+        GTLS_TRY(upload(pl, &pl->prep_off, std::vector<int64_t>{0, n}));
+    }
+    return GTLS_OK;
+}
+
+// The chunk scratch of a plan's own searches (batches bring their own).
+gtls_status ensure_chunk(gtls_plan* pl)
+{
+    if (pl->chunk_ready) return GTLS_OK;
+    DevChunk& dk = pl->dk;
+    const int64_t chunk = dk.chunk;
+    GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.slot, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.sidx, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.rs, chunk * dk.pad_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.ws, chunk * dk.pad_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.wrs, chunk * dk.pad_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.pf, chunk * dk.pad_stride));
+    pl->chunk_ready = true;
     return GTLS_OK;
 }
 
@@ -1208,6 +1399,121 @@ gtls_status collect_profile(gtls_plan* pl, size_t used)
     return GTLS_OK;
 }
 
+// Launch context of one search: a plan's own (one curve) or a batch's.
+struct Ctx {
+    DevSet set{}, set_ref{};
+    DevChunk dk{};
+    int n_lc = 1;
+    int fold_smem = 0;
+    int tile_buf = 0;
+    int n_sm = 0;
+    int median_blocks = 1;   // widest row of the running-median grid
+    int topk_smem = 0;
+    cudaStream_t st = nullptr;
+    int64_t launches = 0, window_launches = 0;
+    gtls_plan* prof = nullptr;   // stage marks (single search with profiling on)
+    size_t ev = 0;
+};
+
+gtls_status stage_mark(Ctx& c, int stage)
+{
+    return c.prof ? mark(c.prof, c.st, stage, c.ev) : GTLS_OK;
+}
+
+// One wave: fold + sort, every window, per-period results.  `counter` must
+// be zero when the window kernel starts (reset here when reset_counter).
+gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, unsigned int* counter,
+                      bool reset_counter, int64_t max_n, int max_kept)
+{
+    const DevSet& ds = ref ? c.set_ref : c.set;
+    k_fold_sort<<<sm.slots, kFoldThreads, c.fold_smem, c.st>>>(ds, sm, c.dk);
+    GTLS_CUDA(cudaGetLastError());
+    GTLS_TRY(stage_mark(c, kStageFold));
+    if (tiled) {
+        if (reset_counter) GTLS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c.st));
+        k_window_tiles<<<c.n_sm, tiles::kThreads, c.tile_buf * (int)sizeof(float), c.st>>>(ds, sm, c.dk,
+                                                                                          c.tile_buf, counter);
+    } else {
+        dim3 grid((unsigned)((max_n + kSearchThreads - 1) / kSearchThreads), (unsigned)max_kept,
+                  (unsigned)sm.slots);
+        k_window_search<<<grid, kSearchThreads, 0, c.st>>>(ds, sm, c.dk);
+    }
+    GTLS_CUDA(cudaGetLastError());
+    GTLS_TRY(stage_mark(c, kStageWindow));
+    k_period_finalize<<<(sm.slots + 127) / 128, 128, 0, c.st>>>(ds, sm, c.dk);
+    GTLS_CUDA(cudaGetLastError());
+    GTLS_TRY(stage_mark(c, kStageFinalize));
+    c.launches += 3;
+    c.window_launches += 1;
+    return GTLS_OK;
+}
+
+// SR, SDE_raw and the median-detrended SDE of every curve.
+gtls_status sr_sde_pass(Ctx& c)
+{
+    k_sr_stats_set<<<c.n_lc, 1024, 0, c.st>>>(c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    k_median_sde_set<<<dim3((unsigned)c.median_blocks, (unsigned)c.n_lc), kMedianThreads, kMedianSmem, c.st>>>(
+        c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    c.launches += 2;
+    return stage_mark(c, kStageSrSde);
+}
+
+// Curve preparation: reset, min(t) and flags, derived arrays and block
+// partials of chi2_0, then the per-curve reduction (flags to flags_out).
+gtls_status prep_pass(Ctx& c, const double* t, const double* y, const double* dy, const int64_t* off_dev,
+                      int64_t max_n, unsigned int* flags_out)
+{
+    k_curve_reset<<<c.n_lc, 32, 0, c.st>>>(c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    const dim3 grid((unsigned)std::max(1, prep_blocks_for(max_n)), (unsigned)c.n_lc);
+    k_curve_minmax<<<grid, 256, 0, c.st>>>(t, y, dy, off_dev, c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    k_curve_prep<<<grid, 256, 0, c.st>>>(t, y, dy, off_dev, c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    k_curve_reduce<<<(c.n_lc + 127) / 128, 128, 0, c.st>>>(dy, off_dev, c.set, 0, c.n_lc, flags_out);
+    GTLS_CUDA(cudaGetLastError());
+    c.launches += 4;
+    return GTLS_OK;
+}
+
+SlotMap single_wave(int first, int cnt, int tiles_per_period, bool from_list)
+{
+    SlotMap sm{};
+    sm.nseg = 1;
+    sm.slots = cnt;
+    sm.items = cnt * tiles_per_period;
+    sm.from_list = from_list ? 1 : 0;
+    sm.seg[0] = WaveSeg{0, first, 0, 0};
+    return sm;
+}
+
+gtls_status check_words(const unsigned int* chk, const std::string& where)
+{
+    if (chk[0] == 0) return GTLS_OK;
+    return fail(GTLS_ERR_INTERNAL, where + "device index check " + std::to_string(chk[0]) + " failed (value " +
+                                       std::to_string(((long long)chk[3] << 32) | chk[1]) + ", limit " +
+                                       std::to_string(chk[2]) + ")");
+}
+
+// Per-period outputs of the plan's last search into caller device arrays.
+gtls_status copy_period_outputs(const gtls_plan* pl, const gtls_period_outputs* per, cudaStream_t st)
+{
+    const DevPeriod& dq = pl->dq;
+    const size_t np_ = (size_t)pl->dp.np;
+    if (per->chi2) GTLS_CUDA(cudaMemcpyAsync(per->chi2, dq.chi2, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    if (per->dur_idx) GTLS_CUDA(cudaMemcpyAsync(per->dur_idx, dq.dur, np_ * 4, cudaMemcpyDeviceToDevice, st));
+    if (per->t0_idx) GTLS_CUDA(cudaMemcpyAsync(per->t0_idx, dq.t0i, np_ * 4, cudaMemcpyDeviceToDevice, st));
+    if (per->depth) GTLS_CUDA(cudaMemcpyAsync(per->depth, dq.depth, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    if (per->t0) GTLS_CUDA(cudaMemcpyAsync(per->t0, dq.t0, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    if (per->sr) GTLS_CUDA(cudaMemcpyAsync(per->sr, dq.sr, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    if (per->sde_raw) GTLS_CUDA(cudaMemcpyAsync(per->sde_raw, dq.sde_raw, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    if (per->sde) GTLS_CUDA(cudaMemcpyAsync(per->sde, dq.sde, np_ * 8, cudaMemcpyDeviceToDevice, st));
+    if (per->refined) GTLS_CUDA(cudaMemcpyAsync(per->refined, dq.refined, np_ * 4, cudaMemcpyDeviceToDevice, st));
+    return GTLS_OK;
+}
+
 gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const double* dy,
                        int64_t n, cudaStream_t st, gtls_result* out,
                        const gtls_period_outputs* per)
@@ -1220,126 +1526,605 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     int dev = -1;
     GTLS_CUDA(cudaGetDevice(&dev));
     if (dev != pl->device) return fail(GTLS_ERR_INVALID_ARG, "current device differs from the plan's device");
+    GTLS_TRY(ensure_chunk(pl));
 
-    DevPlan dp = pl->dp;
-    DevCurve dc = pl->dc;
-    DevChunk dk = pl->dk;
-    DevPeriod dq = pl->dq;
-
+    const DevPlan& dp = pl->dp;
+    const DevChunk& dk = pl->dk;
+    const DevPeriod& dq = pl->dq;
+    Ctx c;
+    c.set = pl->set;
+    c.set_ref = pl->set_ref;
+    c.dk = dk;
+    c.n_lc = 1;
+    c.fold_smem = fold_smem_bytes(h.bucket_log2);
+    c.tile_buf = pl->tile_buf;
+    c.n_sm = pl->n_sm;
+    c.median_blocks = (dp.np + median_outs(dp.median_half) - 1) / median_outs(dp.median_half);
+    c.topk_smem = topk_smem_bytes(dp.np, pl->refine_k);
+    c.st = st;
     pl->profile = gtls_profile{};
-    size_t ev = 0;
-    int64_t launches = 0, window_launches = 0;
-    GTLS_TRY(mark(pl, st, -1, ev));
-    GTLS_CUDA(cudaMemsetAsync(dc.tmin_key, 0xff, sizeof(unsigned long long), st));
-    GTLS_CUDA(cudaMemsetAsync(dc.flags, 0, sizeof(unsigned int), st));
-    GTLS_CUDA(cudaMemsetAsync(dc.check, 0, 4 * sizeof(unsigned int), st));
-    const int prep_blocks = (int)std::min<int64_t>(1024, (n + 255) / 256);
-    k_curve_minmax<<<prep_blocks, 256, 0, st>>>(t, y, dy, n, dc);
-    GTLS_CUDA(cudaGetLastError());
-    k_curve_prep<<<prep_blocks, 256, 0, st>>>(t, y, dy, n, dp.time_exponent, dc);
-    GTLS_CUDA(cudaGetLastError());
-    k_curve_reduce<<<1, 32, 0, st>>>(prep_blocks, dy, dc);
-    GTLS_CUDA(cudaGetLastError());
-    launches += 3;
-    GTLS_TRY(mark(pl, st, kStagePrepare, ev));
+    if (pl->profiling) c.prof = pl;
+
+    GTLS_TRY(stage_mark(c, -1));
+    GTLS_TRY(prep_pass(c, t, y, dy, pl->prep_off, n, pl->dc.flags));
+    GTLS_TRY(stage_mark(c, kStagePrepare));
     unsigned int flags = 0;
-    GTLS_CUDA(cudaMemcpyAsync(&flags, dc.flags, sizeof flags, cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaMemcpyAsync(&flags, pl->dc.flags, sizeof flags, cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaStreamSynchronize(st));
     if (flags & 1u) return fail(GTLS_ERR_INVALID_ARG, "t, y or dy holds a NaN or infinity");
     if (flags & 2u) return fail(GTLS_ERR_INVALID_ARG, "dy must be > 0 everywhere");
 
-    const int fold_smem = fold_smem_bytes(h.bucket_log2);
-    const bool use_tiles = pl->tile_ok && !(flags & 4u);
-    TileCfg tc{pl->tile_buf, pl->tile_len, pl->tile_count};
-    GTLS_CUDA(cudaMemsetAsync(dq.refined, 0, (size_t)dp.np * sizeof(int32_t), st));
-
-    // fold + window search + per-period result for periods p0 .. p0+cnt-1,
-    // or for plist[0 .. cnt) when a list is given
-    auto chunk_pass = [&](const DevPlan& dpx, const TileCfg& tcx, int p0, int cnt,
-                          const int32_t* plist) -> gtls_status {
-        k_fold_sort<<<cnt, kFoldThreads, fold_smem, st>>>(dpx, dc, dk, dq, p0, plist);
-        GTLS_CUDA(cudaGetLastError());
-        GTLS_TRY(mark(pl, st, kStageFold, ev));
-        if (use_tiles) {
-            GTLS_CUDA(cudaMemsetAsync(pl->tile_counter, 0, sizeof(unsigned int), st));
-            k_window_tiles<<<pl->n_sm, tiles::kThreads, pl->tile_buf * (int)sizeof(float), st>>>(
-                dpx, dc, dk, dq, tcx, p0, cnt, pl->tile_counter, plist);
-        } else {
-            dim3 grid((unsigned)((n + kSearchThreads - 1) / kSearchThreads), (unsigned)h.max_kept,
-                      (unsigned)cnt);
-            k_window_search<<<grid, kSearchThreads, 0, st>>>(dpx, dc, dk, dq, p0, plist);
-        }
-        GTLS_CUDA(cudaGetLastError());
-        GTLS_TRY(mark(pl, st, kStageWindow, ev));
-        k_period_finalize<<<(cnt + 127) / 128, 128, 0, st>>>(dpx, dc, dk, dq, p0, cnt, plist);
-        GTLS_CUDA(cudaGetLastError());
-        GTLS_TRY(mark(pl, st, kStageFinalize, ev));
-        launches += 3;
-        window_launches += 1;
-        return GTLS_OK;
-    };
-    const int hwin = h.median_window / 2;
-    const int outs = std::min(1024, kMedianCap - 2 * hwin) & ~31;
-    if (outs < 32) return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
-    auto sr_sde = [&]() -> gtls_status {
-        k_sr_stats<<<1, 1024, 0, st>>>(dp.np, dq);
-        GTLS_CUDA(cudaGetLastError());
-        k_median_sde<<<(dp.np + outs - 1) / outs, kMedianThreads,
-                       kMedianCap * (int)(sizeof(double) + sizeof(int)), st>>>(dp.np, hwin, outs, dq);
-        GTLS_CUDA(cudaGetLastError());
-        launches += 2;
-        GTLS_TRY(mark(pl, st, kStageSrSde, ev));
-        return GTLS_OK;
-    };
+    const bool tiled = pl->tile_ok && !(flags & 4u);
     for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
         const int cnt = std::min<int>(dk.chunk, dp.np - p0);
-        GTLS_TRY(chunk_pass(dp, tc, p0, cnt, nullptr));
+        GTLS_TRY(wave_pass(c, false, single_wave(p0, cnt, pl->tile_count, false), tiled, pl->tile_counter, true,
+                           n, h.max_kept));
     }
-    GTLS_TRY(sr_sde());
+    GTLS_TRY(sr_sde_pass(c));
+    // two-stage T0 search (Sect. 2.5): the refine_k best periods by SDE(P)
+    // again with T0 step 1, then SR / SDE once more (k_topk also clears the
+    // refined flags when refine_k is 0)
+    k_topk<<<1, 1024, c.topk_smem, st>>>(c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    c.launches += 1;
+    GTLS_TRY(stage_mark(c, kStageSrSde));
     const int kref = pl->refine_k;
     if (kref > 0) {
-        // two-stage T0 search (Sect. 2.5): the kref best periods by SDE(P)
-        // again with T0 step 1, then SR / SDE once more
-        k_topk<<<1, 1024, ((dp.np + 31) / 32) * sizeof(unsigned int), st>>>(dp.np, kref, dq, pl->plist);
-        GTLS_CUDA(cudaGetLastError());
-        launches += 1;
-        GTLS_TRY(mark(pl, st, kStageSrSde, ev));
-        TileCfg tc1{pl->tile_buf, pl->tile_len_ref, pl->tile_count_ref};
         for (int r0 = 0; r0 < kref; r0 += dk.chunk) {
             const int cnt = std::min<int>(dk.chunk, kref - r0);
-            GTLS_TRY(chunk_pass(pl->dp_ref, tc1, 0, cnt, pl->plist + r0));
+            GTLS_TRY(wave_pass(c, true, single_wave(r0, cnt, pl->tile_count_ref, true), tiled, pl->tile_counter,
+                               true, n, h.max_kept));
         }
-        GTLS_TRY(sr_sde());
+        GTLS_TRY(sr_sde_pass(c));
     }
-    GTLS_TRY(mark(pl, st, kStageSrSde, ev));
-    k_best<<<1, 1024, 0, st>>>(dp, dc, dq);
+    k_best<<<1, 1024, 0, st>>>(c.set, 0, nullptr, nullptr);
     GTLS_CUDA(cudaGetLastError());
-    launches += 1;
-    if (per) {
-        const size_t np_ = (size_t)dp.np;
-        if (per->chi2) GTLS_CUDA(cudaMemcpyAsync(per->chi2, dq.chi2, np_ * 8, cudaMemcpyDeviceToDevice, st));
-        if (per->dur_idx) GTLS_CUDA(cudaMemcpyAsync(per->dur_idx, dq.dur, np_ * 4, cudaMemcpyDeviceToDevice, st));
-        if (per->t0_idx) GTLS_CUDA(cudaMemcpyAsync(per->t0_idx, dq.t0i, np_ * 4, cudaMemcpyDeviceToDevice, st));
-        if (per->depth) GTLS_CUDA(cudaMemcpyAsync(per->depth, dq.depth, np_ * 8, cudaMemcpyDeviceToDevice, st));
-        if (per->t0) GTLS_CUDA(cudaMemcpyAsync(per->t0, dq.t0, np_ * 8, cudaMemcpyDeviceToDevice, st));
-        if (per->sr) GTLS_CUDA(cudaMemcpyAsync(per->sr, dq.sr, np_ * 8, cudaMemcpyDeviceToDevice, st));
-        if (per->sde_raw) GTLS_CUDA(cudaMemcpyAsync(per->sde_raw, dq.sde_raw, np_ * 8, cudaMemcpyDeviceToDevice, st));
-        if (per->sde) GTLS_CUDA(cudaMemcpyAsync(per->sde, dq.sde, np_ * 8, cudaMemcpyDeviceToDevice, st));
-        if (per->refined)
-            GTLS_CUDA(cudaMemcpyAsync(per->refined, dq.refined, np_ * 4, cudaMemcpyDeviceToDevice, st));
-    }
+    c.launches += 1;
+    GTLS_TRY(stage_mark(c, kStageSrSde));
+    if (per) GTLS_TRY(copy_period_outputs(pl, per, st));
     unsigned int chk[4] = {0, 0, 0, 0};
-    GTLS_CUDA(cudaMemcpyAsync(chk, dc.check, sizeof chk, cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaMemcpyAsync(chk, pl->dc.check, sizeof chk, cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaMemcpyAsync(out, dq.result, sizeof(gtls_result), cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaStreamSynchronize(st));
-    if (chk[0] != 0)
-        return fail(GTLS_ERR_INTERNAL, "device index check " + std::to_string(chk[0]) + " failed (value " +
-                                           std::to_string(((long long)chk[3] << 32) | chk[1]) +
-                                           ", limit " + std::to_string(chk[2]) + ")");
-    out->refined = kref;
-    pl->profile.kernel_launches = launches;
-    pl->profile.window_search_launches = window_launches;
-    if (pl->profiling) GTLS_TRY(collect_profile(pl, ev));
+    GTLS_TRY(check_words(chk, ""));
+    pl->profile.kernel_launches = c.launches;
+    pl->profile.window_search_launches = c.window_launches;
+    if (pl->profiling) GTLS_TRY(collect_profile(pl, c.ev));
+    return GTLS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched search: many light curves, one shared chunk scratch, waves of
+// (curve, period range) segments, replayed from a captured CUDA graph
+// ---------------------------------------------------------------------------
+
+struct BatchWave {
+    SlotMap sm;
+    bool tiled;
+    bool ref;
+    int64_t max_n;
+    int max_kept;
+};
+
+struct BatchCfg {
+    int wave_slots = 0;
+    int tile_buf = 0;
+};
+
+}  // namespace
+
+struct gtls_batch {
+    std::vector<gtls_plan*> plans;
+    int device = -1;
+    int n_lc = 0;
+    std::vector<int64_t> off;          // host offsets (n_lc + 1, from 0)
+    int64_t max_n = 0;
+    int max_kept = 0;
+    int fold_smem = 0, topk_smem = 0, median_blocks = 1, n_sm = 0;
+    int max_slots = 0;                 // chunk scratch slots allocated
+    int tile_buf_max = 0;              // largest staged tile every tiled curve accepts
+    gtls::DevChunk dk{};
+    gtls::DevSet set{}, set_ref{};
+    gtls::DevTiles* d_tiles = nullptr;   // 2 n_lc entries: coarse, refinement
+    int64_t* off_dev = nullptr;
+    unsigned int* flags = nullptr;     // per curve validity flags
+    unsigned int* checks = nullptr;    // 4 words per curve
+    gtls_result* results = nullptr;
+    unsigned int* counters = nullptr;  // one per tiled wave
+    int n_counters = 0;
+    BatchCfg cfg;
+    bool tuned = false;
+    // graph of everything after the curve preparation, for one set of
+    // per-curve kernel classes (uniform dy and tile fit)
+    std::vector<uint8_t> graph_class;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
+    int graph_kernels = 0;
+    int waves = 0;
+    int64_t last_launches = 0;         // kernels of the last search
+    int64_t total_periods = 0;         // coarse plus refinement periods
+    double tuned_rate = 0.0;           // probe window flop/s of the chosen configuration
+    std::vector<gtls::DevTiles> tiles_host;   // 2 n_lc entries
+    std::vector<uint8_t> fits, fits_ref;      // curve fits the tiled kernel at cfg.tile_buf
+    std::vector<void*> allocs;
+    int64_t device_bytes = 0;
+};
+
+namespace {
+
+template <class T>
+gtls_status batch_alloc(gtls_batch* b, T** ptr, size_t count)
+{
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(GTLS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->allocs.push_back(p);
+    b->device_bytes += (int64_t)(count * sizeof(T));
+    *ptr = static_cast<T*>(p);
+    return GTLS_OK;
+}
+
+void batch_release(gtls_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    b->cap_stream = nullptr;
+    for (void* p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+}
+
+// Tile shape of every curve for a staged buffer of `buf` floats; curves
+// whose durations do not fit take the one-thread-per-window kernel.
+void batch_tiles(gtls_batch* b, int buf)
+{
+    b->tiles_host.assign(2 * (size_t)b->n_lc, DevTiles{0, 0});
+    b->fits.assign(b->n_lc, 0);
+    b->fits_ref.assign(b->n_lc, 0);
+    for (int i = 0; i < b->n_lc; ++i) {
+        const gtls_plan* pl = b->plans[i];
+        const PlanHost& h = pl->host;
+        if (!pl->tile_ok) continue;
+        int st_max = 1;
+        bool fits = true, fits1 = true;
+        for (size_t j = 0; j < h.dpts.size(); ++j) {
+            st_max = std::max(st_max, h.stride[j]);
+            const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
+            if ((int64_t)(16 + jrows + 2) * h.stride[j] + 32 > buf) fits = false;
+            if ((int64_t)(16 + h.dpts[j] + 2) + 32 > buf) fits1 = false;
+        }
+        const int64_t len = ((int64_t)buf - h.dmax - 3 * (int64_t)st_max - 96) & ~int64_t(63);
+        const int64_t len1 = ((int64_t)buf - h.dmax - 3 - 96) & ~int64_t(63);
+        if (fits && len >= 64) {
+            b->fits[i] = 1;
+            b->tiles_host[i] = DevTiles{(int32_t)len, (int32_t)((h.n + len - 1) / len)};
+        }
+        if (fits1 && len1 >= 64) {
+            b->fits_ref[i] = 1;
+            b->tiles_host[b->n_lc + i] = DevTiles{(int32_t)len1, (int32_t)((h.n + len1 - 1) / len1)};
+        }
+    }
+}
+
+// Waves over the given (curve, first, count) runs, in order: at most
+// wave_slots slots and kMaxSeg segments each; a run may span waves.
+struct Run {
+    int lc, first, count;
+};
+
+void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, bool ref, int wave_slots,
+                 std::vector<BatchWave>& out)
+{
+    BatchWave w{};
+    auto flush = [&]() {
+        if (w.sm.slots > 0) out.push_back(w);
+        w = BatchWave{};
+        w.tiled = tiled;
+        w.ref = ref;
+        w.sm.from_list = ref ? 1 : 0;
+    };
+    flush();
+    for (const Run& r : runs) {
+        int done = 0;
+        const int tiles_pp = tiled ? b->tiles_host[(ref ? b->n_lc : 0) + r.lc].count : 0;
+        const PlanHost& h = b->plans[r.lc]->host;
+        while (done < r.count) {
+            if (w.sm.slots == wave_slots || w.sm.nseg == kMaxSeg) flush();
+            const int take = std::min(r.count - done, wave_slots - w.sm.slots);
+            WaveSeg g{r.lc, r.first + done, w.sm.slots, w.sm.items};
+            w.sm.seg[w.sm.nseg++] = g;
+            w.sm.slots += take;
+            w.sm.items += take * tiles_pp;
+            w.max_n = std::max<int64_t>(w.max_n, h.n);
+            w.max_kept = std::max(w.max_kept, h.max_kept);
+            done += take;
+        }
+    }
+    flush();
+}
+
+// Per-curve kernel class: 1 = tiled window kernel, 0 = one thread per window.
+std::vector<uint8_t> batch_classes(const gtls_batch* b, const std::vector<unsigned int>& flags)
+{
+    std::vector<uint8_t> c(b->n_lc);
+    for (int i = 0; i < b->n_lc; ++i) c[i] = (b->fits[i] && !(flags[i] & 4u)) ? 1 : 0;
+    return c;
+}
+
+void batch_waves(const gtls_batch* b, const std::vector<uint8_t>& cls, int wave_slots,
+                 std::vector<BatchWave>& coarse, std::vector<BatchWave>& refine)
+{
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool tiled = pass == 0;
+        std::vector<Run> runs, runs_ref;
+        for (int i = 0; i < b->n_lc; ++i) {
+            const gtls_plan* pl = b->plans[i];
+            if ((cls[i] == 1) == tiled) runs.push_back(Run{i, 0, pl->dp.np});
+            const bool tiled_ref = cls[i] == 1 && b->fits_ref[i];
+            if (pl->refine_k > 0 && tiled_ref == tiled) runs_ref.push_back(Run{i, 0, pl->refine_k});
+        }
+        build_waves(b, runs, tiled, false, wave_slots, coarse);
+        build_waves(b, runs_ref, tiled, true, wave_slots, refine);
+    }
+}
+
+Ctx batch_ctx(const gtls_batch* b, cudaStream_t st)
+{
+    Ctx c;
+    c.set = b->set;
+    c.set_ref = b->set_ref;
+    c.dk = b->dk;
+    c.n_lc = b->n_lc;
+    c.fold_smem = b->fold_smem;
+    c.tile_buf = b->cfg.tile_buf;
+    c.n_sm = b->n_sm;
+    c.median_blocks = b->median_blocks;
+    c.topk_smem = b->topk_smem;
+    c.st = st;
+    return c;
+}
+
+gtls_status batch_upload_tiles(gtls_batch* b)
+{
+    GTLS_CUDA(cudaMemcpy(b->d_tiles, b->tiles_host.data(), b->tiles_host.size() * sizeof(DevTiles),
+                         cudaMemcpyHostToDevice));
+    return GTLS_OK;
+}
+
+// Makes sure there is one window-kernel counter per tiled wave.
+gtls_status batch_counters(gtls_batch* b, int tiled_waves)
+{
+    if (tiled_waves <= b->n_counters) return GTLS_OK;
+    const int n = std::max(tiled_waves, 2 * b->n_counters);
+    GTLS_TRY(batch_alloc(b, &b->counters, n));
+    b->n_counters = n;
+    return GTLS_OK;
+}
+
+// Everything after the curve preparation, for the given waves.
+gtls_status batch_enqueue(gtls_batch* b, Ctx& c, const std::vector<BatchWave>& coarse,
+                          const std::vector<BatchWave>& refine, int tiled_waves)
+{
+    GTLS_CUDA(cudaMemsetAsync(b->counters, 0, std::max(1, tiled_waves) * sizeof(unsigned int), c.st));
+    int ci = 0;
+    for (const BatchWave& w : coarse)
+        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, b->counters + (w.tiled ? ci++ : 0), false, w.max_n,
+                           w.max_kept));
+    GTLS_TRY(sr_sde_pass(c));
+    k_topk<<<c.n_lc, 1024, c.topk_smem, c.st>>>(c.set, 0);
+    GTLS_CUDA(cudaGetLastError());
+    c.launches += 1;
+    if (!refine.empty()) {
+        for (const BatchWave& w : refine)
+            GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, b->counters + (w.tiled ? ci++ : 0), false, w.max_n,
+                               w.max_kept));
+        GTLS_TRY(sr_sde_pass(c));
+    }
+    k_best<<<c.n_lc, 1024, 0, c.st>>>(c.set, 0, b->results, b->checks);
+    GTLS_CUDA(cudaGetLastError());
+    c.launches += 1;
+    return GTLS_OK;
+}
+
+int count_tiled(const std::vector<BatchWave>& a, const std::vector<BatchWave>& b)
+{
+    int n = 0;
+    for (const BatchWave& w : a) n += w.tiled ? 1 : 0;
+    for (const BatchWave& w : b) n += w.tiled ? 1 : 0;
+    return n;
+}
+
+gtls_status batch_capture(gtls_batch* b, cudaStream_t st, const std::vector<uint8_t>& cls)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_class.clear();
+    std::vector<BatchWave> coarse, refine;
+    batch_waves(b, cls, b->cfg.wave_slots, coarse, refine);
+    const int tiled_waves = count_tiled(coarse, refine);
+    GTLS_TRY(batch_counters(b, tiled_waves));
+    // captured on the batch's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured); launched on the caller's
+    (void)st;
+    Ctx c = batch_ctx(b, b->cap_stream);
+    GTLS_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    gtls_status s = batch_enqueue(b, c, coarse, refine, tiled_waves);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (s != GTLS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(GTLS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    b->graph = g;
+    GTLS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+    b->graph_class = cls;
+    b->graph_kernels = (int)c.launches;
+    b->waves = (int)coarse.size();
+    return GTLS_OK;
+}
+
+gtls_status batch_check_inputs(const gtls_batch* b, const double* t, const double* y, const double* dy,
+                               const int64_t* offsets)
+{
+    if (!t || !y || !dy || !offsets) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    for (int i = 0; i < b->n_lc; ++i)
+        if (offsets[i + 1] - offsets[i] != b->plans[i]->host.n)
+            return fail(GTLS_ERR_INVALID_ARG, "light curve " + std::to_string(i) + " has " +
+                                                  std::to_string(offsets[i + 1] - offsets[i]) +
+                                                  " points; its plan was made for " +
+                                                  std::to_string(b->plans[i]->host.n));
+    int dev = -1;
+    GTLS_CUDA(cudaGetDevice(&dev));
+    if (dev != b->device) return fail(GTLS_ERR_INVALID_ARG, "current device differs from the batch's device");
+    return GTLS_OK;
+}
+
+// Curve preparation of the whole batch and its validity check (one sync).
+gtls_status batch_prepare(gtls_batch* b, const double* t, const double* y, const double* dy, cudaStream_t st,
+                          std::vector<unsigned int>& flags, int64_t& launches)
+{
+    Ctx c = batch_ctx(b, st);
+    GTLS_TRY(prep_pass(c, t, y, dy, b->off_dev, b->max_n, b->flags));
+    launches += c.launches;
+    flags.assign(b->n_lc, 0u);
+    GTLS_CUDA(cudaMemcpyAsync(flags.data(), b->flags, b->n_lc * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < b->n_lc; ++i) {
+        if (flags[i] & 1u)
+            return fail(GTLS_ERR_INVALID_ARG, "light curve " + std::to_string(i) + ": t, y or dy holds a NaN or infinity");
+        if (flags[i] & 2u)
+            return fail(GTLS_ERR_INVALID_ARG, "light curve " + std::to_string(i) + ": dy must be > 0 everywhere");
+    }
+    return GTLS_OK;
+}
+
+gtls_status batch_search(gtls_batch* b, const double* t, const double* y, const double* dy,
+                         const int64_t* offsets, cudaStream_t st, gtls_result* out)
+{
+    GTLS_TRY(batch_check_inputs(b, t, y, dy, offsets));
+    if (!out) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    const int64_t o0 = offsets[0];
+    std::vector<unsigned int> flags;
+    int64_t launches = 0;
+    GTLS_TRY(batch_prepare(b, t + o0, y + o0, dy + o0, st, flags, launches));
+    const std::vector<uint8_t> cls = batch_classes(b, flags);
+    if (!b->exec || cls != b->graph_class) GTLS_TRY(batch_capture(b, st, cls));
+    GTLS_CUDA(cudaGraphLaunch(b->exec, st));
+    std::vector<unsigned int> chk(4 * (size_t)b->n_lc);
+    GTLS_CUDA(cudaMemcpyAsync(chk.data(), b->checks, chk.size() * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaMemcpyAsync(out, b->results, b->n_lc * sizeof(gtls_result), cudaMemcpyDeviceToHost, st));
+    GTLS_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < b->n_lc; ++i)
+        GTLS_TRY(check_words(&chk[4 * (size_t)i], "light curve " + std::to_string(i) + ": "));
+    b->last_launches = launches + b->graph_kernels;
+    return GTLS_OK;
+}
+
+gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slots, gtls_batch* b)
+{
+    if (n_lc < 1 || n_lc > 65535) return fail(GTLS_ERR_INVALID_ARG, "n_lc must be in [1, 65535]");
+    GTLS_CUDA(cudaGetDevice(&b->device));
+    GTLS_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    b->n_lc = (int)n_lc;
+    b->plans.assign(plans, plans + n_lc);
+    b->off.assign(1, 0);
+    int bucket_log2 = 0, max_np_blocks = 1, topk = 0, buf_max = 1 << 30;
+    int64_t fold_stride = 32, pad_stride = 32;
+    bool any_tiled = false;
+    for (int i = 0; i < b->n_lc; ++i) {
+        gtls_plan* pl = plans[i];
+        if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan in the batch");
+        if (pl->device != b->device) return fail(GTLS_ERR_INVALID_ARG, "plans of a batch must share its device");
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == pl) return fail(GTLS_ERR_INVALID_ARG, "a plan may appear once in a batch");
+        const PlanHost& h = pl->host;
+        b->off.push_back(b->off.back() + h.n);
+        b->max_n = std::max<int64_t>(b->max_n, h.n);
+        b->max_kept = std::max(b->max_kept, h.max_kept);
+        bucket_log2 = std::max(bucket_log2, h.bucket_log2);
+        fold_stride = std::max<int64_t>(fold_stride, pl->dk.fold_stride);
+        pad_stride = std::max<int64_t>(pad_stride, pl->dk.pad_stride);
+        const int mo = median_outs(pl->dp.median_half);
+        max_np_blocks = std::max(max_np_blocks, (pl->dp.np + mo - 1) / mo);
+        topk = std::max(topk, topk_smem_bytes(pl->dp.np, pl->refine_k));
+        if (pl->tile_ok) {
+            buf_max = std::min(buf_max, pl->tile_buf);
+            any_tiled = true;
+        }
+    }
+    b->fold_smem = fold_smem_bytes(bucket_log2);
+    b->topk_smem = topk;
+    b->median_blocks = max_np_blocks;
+    b->n_sm = plans[0]->n_sm;
+    b->tile_buf_max = any_tiled ? buf_max : 0;
+    b->cfg.tile_buf = b->tile_buf_max;
+
+    // chunk scratch shared by all curves: slots of the largest curve's strides
+    DevChunk& dk = b->dk;
+    dk.fold_stride = fold_stride;
+    dk.pad_stride = pad_stride;
+    const int64_t per_slot = fold_stride * (8 + 4 + 4) + pad_stride * (4 + 4 + 4 + 8);
+    const int64_t budget = int64_t(8) << 30;
+    int64_t slots = std::min<int64_t>(4096, std::max<int64_t>(1, budget / per_slot));
+    if (wave_slots > 0) slots = wave_slots;
+    b->max_slots = (int)slots;
+    b->cfg.wave_slots = (int)slots;
+    dk.chunk = (int32_t)slots;
+    GTLS_TRY(batch_alloc(b, &dk.keys, slots * fold_stride));
+    GTLS_TRY(batch_alloc(b, &dk.slot, slots * fold_stride));
+    GTLS_TRY(batch_alloc(b, &dk.sidx, slots * fold_stride));
+    GTLS_TRY(batch_alloc(b, &dk.rs, slots * pad_stride));
+    GTLS_TRY(batch_alloc(b, &dk.ws, slots * pad_stride));
+    GTLS_TRY(batch_alloc(b, &dk.wrs, slots * pad_stride));
+    GTLS_TRY(batch_alloc(b, &dk.pf, slots * pad_stride));
+
+    // per-curve descriptors
+    std::vector<DevPlan> hp(2 * (size_t)n_lc);
+    std::vector<DevCurve> hc(n_lc);
+    std::vector<DevPeriod> hq(n_lc);
+    int64_t total_periods = 0;
+    for (int i = 0; i < b->n_lc; ++i) {
+        hp[i] = plans[i]->dp;
+        hp[n_lc + i] = plans[i]->refine_k > 0 ? plans[i]->dp_ref : plans[i]->dp;
+        hc[i] = plans[i]->dc;
+        hq[i] = plans[i]->dq;
+        total_periods += plans[i]->dp.np + plans[i]->refine_k;
+    }
+    DevPlan* d_plans = nullptr;
+    DevCurve* d_curves = nullptr;
+    DevPeriod* d_outs = nullptr;
+    GTLS_TRY(batch_alloc(b, &d_plans, hp.size()));
+    GTLS_TRY(batch_alloc(b, &d_curves, hc.size()));
+    GTLS_TRY(batch_alloc(b, &d_outs, hq.size()));
+    GTLS_TRY(batch_alloc(b, &b->d_tiles, 2 * (size_t)n_lc));
+    GTLS_CUDA(cudaMemcpy(d_plans, hp.data(), hp.size() * sizeof(DevPlan), cudaMemcpyHostToDevice));
+    GTLS_CUDA(cudaMemcpy(d_curves, hc.data(), hc.size() * sizeof(DevCurve), cudaMemcpyHostToDevice));
+    GTLS_CUDA(cudaMemcpy(d_outs, hq.data(), hq.size() * sizeof(DevPeriod), cudaMemcpyHostToDevice));
+    b->set = DevSet{d_plans, d_curves, d_outs, b->d_tiles};
+    b->set_ref = DevSet{d_plans + n_lc, d_curves, d_outs, b->d_tiles + n_lc};
+    GTLS_TRY(batch_alloc(b, &b->off_dev, b->off.size()));
+    GTLS_CUDA(cudaMemcpy(b->off_dev, b->off.data(), b->off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    GTLS_TRY(batch_alloc(b, &b->flags, n_lc));
+    GTLS_TRY(batch_alloc(b, &b->checks, 4 * (size_t)n_lc));
+    GTLS_TRY(batch_alloc(b, &b->results, n_lc));
+    b->total_periods = total_periods;
+    batch_tiles(b, b->cfg.tile_buf);
+    GTLS_TRY(batch_upload_tiles(b));
+    return GTLS_OK;
+}
+
+// Window-point evaluations of period p of a plan's coarse pass.
+double period_wpe(const PlanHost& h, int p)
+{
+    double w = 0.0;
+    for (int j = h.jlo[p]; j <= h.jhi[p]; ++j) {
+        if (j > h.jlo[p] && h.dpts[j] == h.dpts[j - 1]) continue;
+        w += (double)((h.n + h.stride[j] - 1) / h.stride[j]) * h.dpts[j];
+    }
+    return w;
+}
+
+// Picks the wave size and the staged tile size: every candidate runs the
+// coarse pass of a probe (runs of 256 periods spread over the grids of the
+// first tiled curves) once untimed and twice timed; the score is window-point
+// evaluations per second.
+gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, const double* dy,
+                           const int64_t* offsets, cudaStream_t st)
+{
+    GTLS_TRY(batch_check_inputs(b, t, y, dy, offsets));
+    const int64_t o0 = offsets[0];
+    std::vector<unsigned int> flags;
+    int64_t launches = 0;
+    GTLS_TRY(batch_prepare(b, t + o0, y + o0, dy + o0, st, flags, launches));
+    std::vector<uint8_t> cls = batch_classes(b, flags);
+    std::vector<Run> probe;
+    double probe_wpe = 0.0;
+    for (int i = 0, used = 0; i < b->n_lc && used < 4; ++i) {
+        if (!cls[i]) continue;
+        ++used;
+        const PlanHost& h = b->plans[i]->host;
+        const int np = (int)h.periods.size();
+        for (int k = 0; k < 4; ++k) {
+            const int cnt = std::min(256, np);
+            const int first = std::max(0, std::min(np - cnt, (int)((k + 0.5) * np / 4.0) - cnt / 2));
+            probe.push_back(Run{i, first, cnt});
+            for (int p = first; p < first + cnt; ++p) probe_wpe += period_wpe(h, p);
+        }
+    }
+    if (probe.empty()) return GTLS_OK;   // no curve takes the tiled kernel: nothing to tune
+    std::vector<int> slot_c, buf_c;
+    for (int sc : {b->max_slots, b->max_slots / 2, b->max_slots / 4})
+        if (sc >= 128 && std::find(slot_c.begin(), slot_c.end(), sc) == slot_c.end()) slot_c.push_back(sc);
+    if (slot_c.empty()) slot_c.push_back(b->max_slots);
+    for (int bc : {b->tile_buf_max, 40960, 32768})
+        if (bc <= b->tile_buf_max && bc >= 16384 && std::find(buf_c.begin(), buf_c.end(), bc) == buf_c.end())
+            buf_c.push_back(bc);
+    cudaEvent_t e0, e1;
+    GTLS_CUDA(cudaEventCreate(&e0));
+    GTLS_CUDA(cudaEventCreate(&e1));
+    BatchCfg best = b->cfg;
+    double best_rate = -1.0;
+    gtls_status s = GTLS_OK;
+    for (int bc : buf_c) {
+        batch_tiles(b, bc);
+        bool ok = true;
+        for (const Run& r : probe) ok = ok && b->fits[r.lc];
+        if (!ok) continue;
+        if ((s = batch_upload_tiles(b)) != GTLS_OK) break;
+        for (int sc : slot_c) {
+            std::vector<BatchWave> waves;
+            build_waves(b, probe, true, false, sc, waves);
+            if ((s = batch_counters(b, (int)waves.size())) != GTLS_OK) break;
+            Ctx c = batch_ctx(b, st);
+            c.tile_buf = bc;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 3 && s == GTLS_OK; ++rep) {
+                if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = fail(GTLS_ERR_CUDA, "cudaEventRecord");
+                int ci = 0;
+                for (const BatchWave& w : waves) {
+                    s = wave_pass(c, false, w.sm, true, b->counters + ci++, true, w.max_n, w.max_kept);
+                    if (s != GTLS_OK) break;
+                }
+            }
+            if (s != GTLS_OK) break;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                s = fail(GTLS_ERR_CUDA, "timing the autotuner probe failed");
+                break;
+            }
+            const double rate = 2.0 * probe_wpe / (ms * 1e-3);
+            if (rate > best_rate) {
+                best_rate = rate;
+                best.wave_slots = sc;
+                best.tile_buf = bc;
+            }
+        }
+        if (s != GTLS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = best;
+    batch_tiles(b, best.tile_buf);
+    GTLS_TRY(batch_upload_tiles(b));
+    if (s != GTLS_OK) return s;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_class.clear();
+    b->tuned = true;
+    b->tuned_rate = best_rate;
     return GTLS_OK;
 }
 
@@ -1469,19 +2254,103 @@ gtls_status gtls_search_host(gtls_plan* pl, const double* t, const double* y, co
     return run_search(pl, pl->in_t, pl->in_y, pl->in_dy, n, st, out, nullptr);
 }
 
+gtls_status gtls_batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slots, gtls_batch** out)
+{
+    if (!plans || !out) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    *out = nullptr;
+    if (wave_slots < 0 || wave_slots > 65535) return fail(GTLS_ERR_INVALID_ARG, "wave_slots must be in [0, 65535]");
+    g_last_error.clear();
+    gtls_batch* b = new (std::nothrow) gtls_batch();
+    if (!b) return fail(GTLS_ERR_OOM, "host allocation of the batch failed");
+    gtls_status s;
+    try {
+        s = batch_create(plans, n_lc, wave_slots, b);
+    } catch (const std::bad_alloc&) {
+        s = fail(GTLS_ERR_OOM, "host allocation failed while building the batch");
+    }
+    if (s != GTLS_OK) {
+        batch_release(b);
+        delete b;
+        return s;
+    }
+    *out = b;
+    return GTLS_OK;
+}
+
+gtls_status gtls_batch_search(gtls_batch* b, const double* t, const double* y, const double* dy,
+                              const int64_t* offsets, void* stream, gtls_result* out)
+{
+    if (!b) return fail(GTLS_ERR_INVALID_ARG, "null batch");
+    g_last_error.clear();
+    try {
+        return batch_search(b, t, y, dy, offsets, static_cast<cudaStream_t>(stream), out);
+    } catch (const std::bad_alloc&) {
+        return fail(GTLS_ERR_OOM, "host allocation failed during the batch search");
+    }
+}
+
+gtls_status gtls_batch_autotune(gtls_batch* b, const double* t, const double* y, const double* dy,
+                                const int64_t* offsets, void* stream)
+{
+    if (!b) return fail(GTLS_ERR_INVALID_ARG, "null batch");
+    g_last_error.clear();
+    try {
+        return batch_autotune(b, t, y, dy, offsets, static_cast<cudaStream_t>(stream));
+    } catch (const std::bad_alloc&) {
+        return fail(GTLS_ERR_OOM, "host allocation failed during autotuning");
+    }
+}
+
+gtls_status gtls_batch_get_info(const gtls_batch* b, gtls_batch_info* o)
+{
+    if (!b || !o) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    std::memset(o, 0, sizeof *o);
+    o->n_lc = b->n_lc;
+    o->n_points = b->off.back();
+    for (const gtls_plan* pl : b->plans) {
+        o->n_periods += pl->dp.np;
+        o->wpe += pl->host.wpe;
+    }
+    o->waves = b->waves;
+    o->wave_slots = b->cfg.wave_slots;
+    o->tile_floats = b->cfg.tile_buf;
+    o->graph_kernels = b->graph_kernels;
+    o->last_launches = b->last_launches;
+    o->device_bytes = b->device_bytes;
+    o->tuned = b->tuned ? 1 : 0;
+    o->tuned_flops = b->tuned_rate;
+    return GTLS_OK;
+}
+
+gtls_status gtls_batch_get_period_outputs(const gtls_batch* b, int64_t lc, const gtls_period_outputs* per,
+                                          void* stream)
+{
+    if (!b || !per) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
+    if (lc < 0 || lc >= b->n_lc) return fail(GTLS_ERR_INVALID_ARG, "light curve index out of range");
+    return copy_period_outputs(b->plans[(size_t)lc], per, static_cast<cudaStream_t>(stream));
+}
+
+void gtls_batch_destroy(gtls_batch* b)
+{
+    if (!b) return;
+    int cur = -1;
+    const bool switch_dev = cudaGetDevice(&cur) == cudaSuccess && cur != b->device && b->device >= 0;
+    if (switch_dev) cudaSetDevice(b->device);
+    batch_release(b);
+    if (switch_dev) cudaSetDevice(cur);
+    delete b;
+}
+
 gtls_status gtls_search_batch(gtls_plan* const* plans, int64_t n_lc, const double* t, const double* y,
                               const double* dy, const int64_t* offsets, void* stream, gtls_result* out)
 {
-    if (!plans || !offsets || !out || n_lc < 0) return fail(GTLS_ERR_INVALID_ARG, "null pointer argument");
-    g_last_error.clear();
-    for (int64_t i = 0; i < n_lc; ++i) {
-        const int64_t a = offsets[i], b = offsets[i + 1];
-        if (b < a) return fail(GTLS_ERR_INVALID_ARG, "offsets must be non-decreasing");
-        gtls_status s = run_search(plans[i], t + a, y + a, dy + a, b - a,
-                                   static_cast<cudaStream_t>(stream), &out[i], nullptr);
-        if (s != GTLS_OK) return fail(s, "light curve " + std::to_string(i) + ": " + g_last_error);
-    }
-    return GTLS_OK;
+    gtls_batch* b = nullptr;
+    GTLS_TRY(gtls_batch_create(plans, n_lc, 0, &b));
+    const gtls_status s = gtls_batch_search(b, t, y, dy, offsets, stream, out);
+    const std::string err = g_last_error;
+    gtls_batch_destroy(b);
+    g_last_error = err;
+    return s;
 }
 
 void gtls_plan_destroy(gtls_plan* pl)

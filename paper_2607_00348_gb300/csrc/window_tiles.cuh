@@ -82,7 +82,8 @@ __host__ __device__ inline bool variant_colpair(int v) { return v >= kCol16; }
 
 struct DurTask {
     int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total, jrows;
-    long long toff, t2off;    // template offsets (floats / float2 pairs)
+    const float* tg;          // template of the duration (global, zero padded)
+    const float2* tg2;        // its pair table (pair variants)
     float inv_sum_t, sum_t2;  // 2^-40 / sum_k s_k and sum_k s_k^2
     float inv_sum_t_f;        // 1 / sum_k s_k
 };

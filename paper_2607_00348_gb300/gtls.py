@@ -2,6 +2,7 @@
 
 The names follow the C ABI in ``include/gtls.h``: ``gtls_plan_create``,
 ``gtls_search``, ``gtls_search_host``, ``gtls_search_batch``,
+``gtls_batch_create`` / ``gtls_batch_search`` / ``gtls_batch_autotune``,
 ``gtls_plan_destroy``.  Every step of the search runs in the library's CUDA
 kernels; this module never computes any part of it.  Loading fails loudly
 when the library has not been built.
@@ -88,6 +89,19 @@ class PeriodOutputs(ctypes.Structure):
                 ("refined", ctypes.c_void_p)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_lc", ctypes.c_int64), ("n_points", ctypes.c_int64),
+                ("n_periods", ctypes.c_int64), ("wpe", ctypes.c_double),
+                ("waves", ctypes.c_int32), ("wave_slots", ctypes.c_int32),
+                ("tile_floats", ctypes.c_int32), ("graph_kernels", ctypes.c_int32),
+                ("last_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("tuned", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("tuned_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
 # (name, restype, argtypes) of every symbol declared in include/gtls.h
 SIGNATURES = [
     ("gtls_plan_params_default", None, [ctypes.POINTER(PlanParams)]),
@@ -104,6 +118,18 @@ SIGNATURES = [
     ("gtls_search_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          c_int64_p, ctypes.c_void_p, ctypes.POINTER(Result)]),
+    ("gtls_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    ("gtls_batch_search", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, c_int64_p, ctypes.c_void_p,
+                                         ctypes.POINTER(Result)]),
+    ("gtls_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, c_int64_p, ctypes.c_void_p]),
+    ("gtls_batch_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchInfo)]),
+    ("gtls_batch_get_period_outputs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64,
+                                                     ctypes.POINTER(PeriodOutputs),
+                                                     ctypes.c_void_p]),
+    ("gtls_batch_destroy", None, [ctypes.c_void_p]),
     ("gtls_plan_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("gtls_plan_get_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     ("gtls_sr_sde_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
@@ -291,6 +317,60 @@ def search_batch(plans, t, y, dy, offsets, stream=None):
     _check(lib.gtls_search_batch(arr, n_lc, _ptr(t), _ptr(y), _ptr(dy),
                                  offs.ctypes.data_as(c_int64_p), _stream_handle(stream), out))
     return list(out)
+
+
+class Batch:
+    """gtls_batch: many light curves (one plan each) searched in waves of a
+    shared chunk scratch, replayed from a captured CUDA graph."""
+
+    def __init__(self, plans, wave_slots: int = 0):
+        self._lib = load()
+        self.plans = list(plans)  # keep the plans alive as long as the batch
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        self.handle = ctypes.c_void_p()
+        _check(self._lib.gtls_batch_create(arr, len(self.plans), int(wave_slots),
+                                           ctypes.byref(self.handle)))
+
+    @staticmethod
+    def _offsets(offsets):
+        return np.ascontiguousarray(offsets, np.int64)
+
+    def search(self, t, y, dy, offsets, stream=None):
+        offs = self._offsets(offsets)
+        out = (Result * len(self.plans))()
+        _check(self._lib.gtls_batch_search(self.handle, _ptr(t), _ptr(y), _ptr(dy),
+                                           offs.ctypes.data_as(c_int64_p),
+                                           _stream_handle(stream), out))
+        return list(out)
+
+    def autotune(self, t, y, dy, offsets, stream=None):
+        offs = self._offsets(offsets)
+        _check(self._lib.gtls_batch_autotune(self.handle, _ptr(t), _ptr(y), _ptr(dy),
+                                             offs.ctypes.data_as(c_int64_p),
+                                             _stream_handle(stream)))
+        return self.info()
+
+    def period_outputs(self, lc: int, per_period: dict, stream=None):
+        """Copy curve lc's per-period outputs of the last search into device tensors."""
+        po = PeriodOutputs(*[_ptr(per_period.get(f)) for f, _ in PeriodOutputs._fields_])
+        _check(self._lib.gtls_batch_get_period_outputs(self.handle, int(lc), ctypes.byref(po),
+                                                       _stream_handle(stream)))
+
+    def info(self) -> BatchInfo:
+        bi = BatchInfo()
+        _check(self._lib.gtls_batch_get_info(self.handle, ctypes.byref(bi)))
+        return bi
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.gtls_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sr_sde_noalloc(chi2, sde, sr=None, sde_raw=None, median_window=0, stream=None):

@@ -32,6 +32,26 @@ def oracle_plan_for(n, baseline, cfg=None, **kw):
                     periods_days=cfg.get("periods_days"))
 
 
+def period_buffers(npd):
+    import torch
+    dev = torch.device("cuda:0")
+    f64 = dict(dtype=torch.float64, device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    return dict(chi2=torch.empty(npd, **f64), dur_idx=torch.empty(npd, **i32),
+                t0_idx=torch.empty(npd, **i32), depth=torch.empty(npd, **f64),
+                t0=torch.empty(npd, **f64), sr=torch.empty(npd, **f64),
+                sde_raw=torch.empty(npd, **f64), sde=torch.empty(npd, **f64),
+                refined=torch.empty(npd, **i32))
+
+
+def batch_outputs(batch, lc, npd):
+    import torch
+    outs = period_buffers(npd)
+    batch.period_outputs(lc, outs)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in outs.items()}
+
+
 def gpu_search(plan, t, y, dy):
     import torch
     dev = torch.device("cuda:0")

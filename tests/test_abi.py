@@ -70,10 +70,11 @@ def _c_layout():
 #include <stddef.h>
 #include "gtls.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(gtls_plan_params), sizeof(gtls_plan_info),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gtls_plan_params), sizeof(gtls_plan_info),
          sizeof(gtls_result), sizeof(gtls_period_outputs),
          offsetof(gtls_plan_params, periods_days), offsetof(gtls_result, period_idx),
-         offsetof(gtls_plan_info, wpe));
+         offsetof(gtls_plan_info, wpe), sizeof(gtls_batch_info),
+         offsetof(gtls_batch_info, last_launches), offsetof(gtls_batch_info, tuned_flops));
   return 0;
 }
 '''
@@ -92,5 +93,6 @@ def test_ctypes_structs_match_the_header_layout():
     want = [ctypes.sizeof(binding.PlanParams), ctypes.sizeof(binding.PlanInfo),
             ctypes.sizeof(binding.Result), ctypes.sizeof(binding.PeriodOutputs),
             binding.PlanParams.periods_days.offset, binding.Result.period_idx.offset,
-            binding.PlanInfo.wpe.offset]
+            binding.PlanInfo.wpe.offset, ctypes.sizeof(binding.BatchInfo),
+            binding.BatchInfo.last_launches.offset, binding.BatchInfo.tuned_flops.offset]
     assert got == want

@@ -1,0 +1,127 @@
+"""Batched search (gtls_batch_*): many curves of uneven length in waves of a
+shared chunk scratch, replayed from a captured CUDA graph.
+
+Every result of a batch must equal the single-curve search of the same
+curve bit for bit (same kernels, same arithmetic per window), whatever the
+wave size, the staged tile size the autotuner picks, the mix of uniform and
+per-point dy, or the refinement stage.  The single-curve path is itself
+checked against the oracle in test_gpu_parity.py; one batch curve is checked
+against the oracle here as well.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import search as osr
+
+from . import gpu_helpers as gh
+
+pytestmark = pytest.mark.gpu
+
+
+def _curves():
+    """(t, y, dy, cfg) of a mixed batch: two 1440-point curves (one with the
+    refinement stage), two Kepler-like curves of uneven length and a
+    1001-point curve with per-point dy."""
+    out = []
+    for s, k in ((0, 50), (5, 0)):
+        lc = synth.short_white(seed=s)
+        out.append((lc.t, lc.y, lc.dy, dict(lc.search, refine_periods=k)))
+    for lc in synth.batch_kepler_like(2, seed=7, n_min=8000, n_max=14000):
+        out.append((lc.t, lc.y, lc.dy, dict(lc.search)))
+    rng = np.random.default_rng(2)
+    n = 1001
+    t = np.sort(rng.uniform(0.0, 40.0, n))
+    y = 1.0 + rng.normal(0, 1e-3, n)
+    y[rng.random(n) < 0.05] -= 4e-3
+    dy = rng.uniform(5e-4, 3e-3, n)
+    out.append((t, y, dy, dict(period_min_days=0.6, period_max_days=12.0)))
+    return out
+
+
+def _packed(curves):
+    import torch
+    dev = torch.device("cuda:0")
+    cat = lambda k: torch.as_tensor(np.concatenate([c[k] for c in curves]), dtype=torch.float64,
+                                    device=dev)
+    offs = np.cumsum([0] + [c[0].size for c in curves]).astype(np.int64)
+    return cat(0), cat(1), cat(2), offs
+
+
+def _plans(curves):
+    return [gh.plan_for(c[0].size, float(c[0].max() - c[0].min()), c[3]) for c in curves]
+
+
+def _same(batch, plans, res, singles):
+    for i, (r, (rs, outs)) in enumerate(zip(res, singles)):
+        assert r.as_dict() == rs.as_dict(), i
+        got = gh.batch_outputs(batch, i, plans[i].n_periods)
+        for k in ("chi2", "dur_idx", "t0_idx", "depth", "t0", "sr", "sde_raw", "sde", "refined"):
+            assert np.array_equal(got[k], outs[k]), (i, k)
+
+
+def test_batch_equals_single_curve_searches():
+    import paper_2607_00348_gb300 as pkg
+    curves = _curves()
+    plans = _plans(curves)
+    singles = [gh.gpu_search(p, c[0], c[1], c[2]) for p, c in zip(plans, curves)]
+    assert singles[0][0].refined == 50 and singles[4][0].uniform_dy == 0
+    t, y, dy, offs = _packed(curves)
+    # a small wave size makes waves span several curves and curves span waves
+    batch = pkg.Batch(plans, wave_slots=700)
+    for _ in range(2):   # capture, then replay of the graph
+        res = batch.search(t, y, dy, offs)
+        _same(batch, plans, res, singles)
+    info = batch.info()
+    assert info.waves > 1 and info.graph_kernels > 3 * info.waves
+    assert info.n_lc == len(curves) and info.n_points == offs[-1]
+    tuned = batch.autotune(t, y, dy, offs)
+    assert tuned.tuned == 1 and tuned.tuned_flops > 0
+    res = batch.search(t, y, dy, offs)
+    _same(batch, plans, res, singles)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_curve_matches_oracle_on_sampled_periods():
+    import paper_2607_00348_gb300 as pkg
+    curves = _curves()[2:4]
+    plans = _plans(curves)
+    t, y, dy, offs = _packed(curves)
+    batch = pkg.Batch(plans)
+    batch.search(t, y, dy, offs)
+    for i, (tt, yy, dd, cfg) in enumerate(curves):
+        op = gh.oracle_plan_for(tt.size, float(tt.max() - tt.min()), cfg)
+        npd = op.periods.size
+        sel = np.unique(np.linspace(0, npd - 1, 12).astype(int))
+        r_or = osr.search_periods(op, tt, yy, dd, sel)
+        got = gh.batch_outputs(batch, i, npd)
+        np.testing.assert_allclose(got["chi2"][sel], r_or.chi2, rtol=1e-5, atol=0)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_reports_the_bad_curve_and_stays_usable():
+    import paper_2607_00348_gb300 as pkg
+    curves = _curves()[:3]
+    plans = _plans(curves)
+    t, y, dy, offs = _packed(curves)
+    batch = pkg.Batch(plans)
+    y_bad = y.clone()
+    y_bad[int(offs[2]) + 17] = float("nan")
+    with pytest.raises(pkg.GtlsError, match="light curve 2.*NaN"):
+        batch.search(t, y_bad, dy, offs)
+    bad_offs = offs.copy()
+    bad_offs[1] += 1
+    with pytest.raises(pkg.GtlsError, match="INVALID_ARG"):
+        batch.search(t, y, dy, bad_offs)
+    res = batch.search(t, y, dy, offs)
+    assert abs(res[0].period - 3.7) < 0.05
+    batch.close()
+    with pytest.raises(pkg.GtlsError, match="once"):
+        pkg.Batch([plans[0], plans[0]])
+    for p in plans:
+        p.close()
