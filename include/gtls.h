@@ -301,6 +301,81 @@ gtls_status gtls_sr_sde_noalloc(const double* chi2, int64_t n_periods, int32_t m
                                 void* stream, double* sr_out, double* sde_raw_out, double* sde_out,
                                 int64_t* best_idx, double* best_sde);
 
+/*
+ * Learned period proposal (no counterpart in the paper).  A 1D CNN reads a
+ * light curve binned in time (4096 bins, not folded) and predicts, for each
+ * of 128 regions that split [0.5, 1024) days evenly in log P, the largest
+ * SR(P) that the search finds there; the full search then runs only on the
+ * trial periods of the best regions (gtls_proposal_periods), falling back to
+ * the whole grid when the prediction is not confident (caller's choice).
+ *
+ * Network: input x[B][4096]; six 'same' 1D convolutions (taps 7, 5, 5, 5,
+ * 5, 5; 64 output channels) each with bias, ReLU and max-pooling by 2
+ * (pair (2j, 2j+1), the first wins ties); a linear head from the 64 x 64
+ * features (feature = position * 64 + channel) to 128 logits; scores =
+ * sigmoid(logits).  Loss: masked mean logistic loss with soft targets,
+ *   L = sum mask (softplus(z) - target z) / max(1, sum mask).
+ * Parameters: one FP32 vector of gtls_cnn_param_count() floats in the order
+ * w0 b0 w1 b1 ... w5 b5 wh bh, with conv weights [64][taps][in channels],
+ * head weights [128][4096].  The contractions run as BF16 tensor-core GEMMs
+ * with FP32 accumulation (activations stored in BF16); master parameters,
+ * gradients and Adam moments are FP32.
+ * Device pointers below are arrays on the network's device; the network is
+ * not thread-safe (one call at a time).
+ */
+typedef struct gtls_cnn gtls_cnn;
+
+int64_t gtls_cnn_param_count(void);
+
+/* max_batch in [1, 4096]; params: host FP32 vector (NULL = zeros). */
+gtls_status gtls_cnn_create(int32_t max_batch, const float* params, gtls_cnn** out);
+gtls_status gtls_cnn_get_params(const gtls_cnn* cnn, float* params);
+/* Replace the parameters (host vector) and reset the Adam state. */
+gtls_status gtls_cnn_set_params(gtls_cnn* cnn, const float* params);
+
+/*
+ * Network input of n_lc <= max_batch light curves packed as in
+ * gtls_batch_search (t, y, dy device arrays; offsets host, n_lc + 1):
+ * x[i][b] (device, n_lc x 4096 floats) = sum(w r) / sqrt(sum w) over the
+ * points of curve i with floor((t - t_min) / (t_max - t_min) * 4096) = b
+ * (the last point in bin 4095), r = 1 - y, w = 1/dy^2; 0 for empty bins.
+ * Synchronises `stream`.
+ */
+gtls_status gtls_cnn_bin(gtls_cnn* cnn, const double* t, const double* y, const double* dy,
+                         const int64_t* offsets, int64_t n_lc, float* x, void* stream);
+
+/* logits / scores: device [batch][128] floats, each nullable. */
+gtls_status gtls_cnn_forward(gtls_cnn* cnn, const float* x, int32_t batch, float* logits,
+                             float* scores, void* stream);
+
+/*
+ * Loss and gradient for targets / mask (device [batch][128]) without an
+ * update: grad (host, gtls_cnn_param_count floats, nullable), loss (host,
+ * nullable).  Synchronises `stream`.
+ */
+gtls_status gtls_cnn_gradient(gtls_cnn* cnn, const float* x, const float* target, const float* mask,
+                              int32_t batch, float* grad, double* loss, void* stream);
+
+/* Gradient and one Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr). */
+gtls_status gtls_cnn_train_step(gtls_cnn* cnn, const float* x, const float* target, const float* mask,
+                                int32_t batch, float lr, double* loss, void* stream);
+
+void gtls_cnn_destroy(gtls_cnn* cnn);
+
+/*
+ * Host helpers of the proposal.  Region of a period: floor(128 log(P/0.5) /
+ * log(2048)); periods outside [0.5, 1024) belong to none.
+ * gtls_region_targets: target[r] = largest sr[i] of region r's periods,
+ *   mask[r] = 1 where region r holds a period (host arrays of 128 floats).
+ * gtls_proposal_periods: indices (ascending, into idx of n_periods capacity)
+ *   of the periods inside the ceil(frac x regions holding a period) regions
+ *   of largest score (ties: lower region first); *n_idx receives the count.
+ */
+gtls_status gtls_region_targets(const double* periods, const double* sr, int64_t n_periods,
+                                float* target, float* mask);
+gtls_status gtls_proposal_periods(const double* periods, int64_t n_periods, const float* scores,
+                                  double frac, int64_t* idx, int64_t* n_idx);
+
 /* Release the plan's device and host memory (NULL is a no-op). */
 void gtls_plan_destroy(gtls_plan* plan);
 

@@ -150,17 +150,20 @@ def conv_same(x, w, b):
     return out
 
 
-def forward(params, x):
+def forward(params, x, store=None):
     """Activations of every layer for inputs x[n, n_bins]; returns the
-    logits z[n, N_REG] and a cache for backward."""
-    a = np.asarray(x, np.float64)[:, :, None]
+    logits z[n, N_REG] and a cache for backward.  `store` (optional) maps
+    the input and every pooled activation to the precision they are stored
+    in (identity by default: FP64 throughout)."""
+    keep = store if store is not None else (lambda v: v)
+    a = keep(np.asarray(x, np.float64))[:, :, None]
     cache = []
     for i in range(N_CONV):
         pre = conv_same(a, params[f"w{i}"], params[f"b{i}"])
         act = np.maximum(pre, 0.0)
         n, length, c = act.shape
         pair = act.reshape(n, length // 2, 2, c)
-        pooled = pair.max(axis=2)
+        pooled = keep(pair.max(axis=2))
         arg = pair.argmax(axis=2)             # first of equal pair members
         cache.append((a, pre, arg))
         a = pooled

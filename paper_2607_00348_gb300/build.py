@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libgtls.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["search.cu", "plan_host.cpp"]
+SOURCES = ["search.cu", "plan_host.cpp", "proposal.cu"]
 
 
 def _nvcc() -> str:

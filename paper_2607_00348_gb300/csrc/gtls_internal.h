@@ -125,6 +125,10 @@ struct SlotMap {
     WaveSeg seg[kMaxSeg];
 };
 
+// Records `msg` as the calling thread's last error and returns s (shared by
+// the translation units behind the C ABI).
+gtls_status set_error(gtls_status s, const std::string& msg);
+
 }  // namespace gtls
 
 struct gtls_plan {

@@ -38,6 +38,15 @@ gtls_status fail(gtls_status s, const std::string& msg)
     return s;
 }
 
+}  // namespace
+
+gtls_status gtls::set_error(gtls_status s, const std::string& msg)
+{
+    return fail(s, msg);
+}
+
+namespace {
+
 #define GTLS_CUDA(call)                                                                   \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \

@@ -135,6 +135,27 @@ SIGNATURES = [
     ("gtls_sr_sde_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, c_int64_p, c_double_p]),
+    ("gtls_cnn_param_count", ctypes.c_int64, []),
+    ("gtls_cnn_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    ("gtls_cnn_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("gtls_cnn_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("gtls_cnn_bin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, c_int64_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    ("gtls_cnn_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("gtls_cnn_gradient", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                         c_double_p, ctypes.c_void_p]),
+    ("gtls_cnn_train_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                           c_double_p, ctypes.c_void_p]),
+    ("gtls_cnn_destroy", None, [ctypes.c_void_p]),
+    ("gtls_region_targets", ctypes.c_int, [c_double_p, c_double_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    ("gtls_proposal_periods", ctypes.c_int, [c_double_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_double, c_int64_p, c_int64_p]),
     ("gtls_plan_destroy", None, [ctypes.c_void_p]),
     ("gtls_last_error", ctypes.c_char_p, []),
     ("gtls_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -388,3 +409,96 @@ def sr_sde_noalloc(chi2, sde, sr=None, sde_raw=None, median_window=0, stream=Non
                                    _ptr(sr), _ptr(sde_raw), _ptr(sde), ctypes.byref(bi),
                                    ctypes.byref(bs)))
     return int(bi.value), float(bs.value)
+
+
+N_BINS = 4096
+N_REG = 128
+
+
+class Cnn:
+    """gtls_cnn: the learned period proposal network (BF16 tensor-core kernels)."""
+
+    def __init__(self, max_batch: int, params=None):
+        self._lib = load()
+        self.max_batch = int(max_batch)
+        self.n_params = int(self._lib.gtls_cnn_param_count())
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(params, np.float32)
+            if buf.size != self.n_params:
+                raise ValueError("parameter vector has the wrong size")
+        self.handle = ctypes.c_void_p()
+        _check(self._lib.gtls_cnn_create(self.max_batch,
+                                         buf.ctypes.data if buf is not None else None,
+                                         ctypes.byref(self.handle)))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(self._lib.gtls_cnn_get_params(self.handle, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        buf = np.ascontiguousarray(params, np.float32)
+        if buf.size != self.n_params:
+            raise ValueError("parameter vector has the wrong size")
+        _check(self._lib.gtls_cnn_set_params(self.handle, buf.ctypes.data))
+
+    def bin(self, t, y, dy, offsets, x, stream=None):
+        offs = np.ascontiguousarray(offsets, np.int64)
+        _check(self._lib.gtls_cnn_bin(self.handle, _ptr(t), _ptr(y), _ptr(dy),
+                                      offs.ctypes.data_as(c_int64_p), offs.size - 1, _ptr(x),
+                                      _stream_handle(stream)))
+
+    def forward(self, x, batch, logits=None, scores=None, stream=None):
+        _check(self._lib.gtls_cnn_forward(self.handle, _ptr(x), int(batch), _ptr(logits),
+                                          _ptr(scores), _stream_handle(stream)))
+
+    def gradient(self, x, target, mask, batch, stream=None):
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(self._lib.gtls_cnn_gradient(self.handle, _ptr(x), _ptr(target), _ptr(mask),
+                                           int(batch), g.ctypes.data, ctypes.byref(loss),
+                                           _stream_handle(stream)))
+        return g, float(loss.value)
+
+    def train_step(self, x, target, mask, batch, lr, stream=None) -> float:
+        loss = ctypes.c_double(0.0)
+        _check(self._lib.gtls_cnn_train_step(self.handle, _ptr(x), _ptr(target), _ptr(mask),
+                                             int(batch), float(lr), ctypes.byref(loss),
+                                             _stream_handle(stream)))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.gtls_cnn_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def region_targets(periods, sr):
+    """gtls_region_targets on host arrays: (target[128], mask[128])."""
+    lib = load()
+    p = np.ascontiguousarray(periods, np.float64)
+    s = np.ascontiguousarray(sr, np.float64)
+    tgt = np.empty(N_REG, np.float32)
+    mask = np.empty(N_REG, np.float32)
+    _check(lib.gtls_region_targets(p.ctypes.data_as(c_double_p), s.ctypes.data_as(c_double_p),
+                                   p.size, tgt.ctypes.data, mask.ctypes.data))
+    return tgt, mask
+
+
+def proposal_periods(periods, scores, frac) -> np.ndarray:
+    """gtls_proposal_periods on host arrays: indices of the proposed periods."""
+    lib = load()
+    p = np.ascontiguousarray(periods, np.float64)
+    sc = np.ascontiguousarray(scores, np.float32)
+    idx = np.empty(max(1, p.size), np.int64)
+    n = ctypes.c_int64(0)
+    _check(lib.gtls_proposal_periods(p.ctypes.data_as(c_double_p), p.size, sc.ctypes.data,
+                                     float(frac), idx.ctypes.data_as(c_int64_p), ctypes.byref(n)))
+    return idx[:n.value].copy()

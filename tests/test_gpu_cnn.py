@@ -1,0 +1,134 @@
+"""Proposal-network kernels (BF16 tensor-core GEMMs, FP32 accumulation)
+against the FP64 reference in oracle/cnn.py.
+
+The reference runs on the same BF16-rounded parameters and stores its input
+and pooled activations in BF16 too (the `store` hook), so that the pooling
+decisions and the stored values are taken in the kernels' precision; what
+remains is FP32 vs FP64 accumulation and the BF16 rounding of the
+gradients inside the backward GEMMs.  Tolerances: logits within 1e-2 of the
+largest |logit|; every parameter tensor's gradient within 3e-2 relative
+(L2 norm); binning within 1e-6 relative.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    """Round to bfloat16 (nearest even) and back to float64."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _setup(seed, batch):
+    rng = np.random.default_rng(seed)
+    params = cnn.init_params(seed)
+    for name in params:
+        if name.startswith("b"):
+            params[name] = rng.normal(0, 0.05, params[name].shape)
+    flat = cnn.flatten(params).astype(np.float32)
+    x = rng.normal(0, 1.5, (batch, cnn.N_BINS))
+    x[:, 1000:1003] += 6.0
+    tgt = rng.uniform(size=(batch, cnn.N_REG))
+    mask = (rng.uniform(size=(batch, cnn.N_REG)) < 0.7).astype(float)
+    # the reference sees the parameters as the GEMMs do: weights in BF16,
+    # biases in FP32
+    p_ref = cnn.unflatten(flat.astype(np.float64))
+    for name in p_ref:
+        if name.startswith("w"):
+            p_ref[name] = bf16(p_ref[name])
+    return flat, x, tgt, mask, p_ref
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float32,
+                           device=torch.device("cuda:0"))
+
+
+def test_forward_matches_reference():
+    import torch
+    import paper_2607_00348_gb300 as pkg
+    flat, x, tgt, mask, p_ref = _setup(0, 5)
+    net = pkg.Cnn(8, flat)
+    xd = _dev(x)
+    logits = torch.empty((5, cnn.N_REG), dtype=torch.float32, device=xd.device)
+    scores = torch.empty_like(logits)
+    net.forward(xd, 5, logits=logits, scores=scores)
+    torch.cuda.synchronize()
+    z_ref, _ = cnn.forward(p_ref, bf16(x), store=bf16)
+    z = logits.cpu().numpy()
+    np.testing.assert_allclose(z, z_ref, rtol=0, atol=1e-2 * np.abs(z_ref).max())
+    np.testing.assert_allclose(scores.cpu().numpy(), 1 / (1 + np.exp(-z)), rtol=1e-5, atol=1e-6)
+    net.close()
+
+
+def test_gradients_match_reference():
+    import paper_2607_00348_gb300 as pkg
+    flat, x, tgt, mask, p_ref = _setup(1, 6)
+    net = pkg.Cnn(8, flat)
+    g, loss = net.gradient(_dev(x), _dev(tgt), _dev(mask), 6)
+    z_ref, cache = cnn.forward(p_ref, bf16(x), store=bf16)
+    loss_ref, dz = cnn.loss_and_dz(z_ref, tgt, mask)
+    g_ref = cnn.backward(p_ref, cache, dz)
+    assert loss == pytest.approx(loss_ref, rel=1e-3)
+    got = cnn.unflatten(g.astype(np.float64))
+    for name, _ in cnn.param_shapes():
+        err = np.linalg.norm(got[name] - g_ref[name]) / max(np.linalg.norm(g_ref[name]), 1e-30)
+        assert err < 3e-2, (name, err)
+    net.close()
+
+
+def test_adam_step_applies_the_gradient():
+    import paper_2607_00348_gb300 as pkg
+    flat, x, tgt, mask, _ = _setup(2, 4)
+    net = pkg.Cnn(4, flat)
+    g, _ = net.gradient(_dev(x), _dev(tgt), _dev(mask), 4)
+    net.train_step(_dev(x), _dev(tgt), _dev(mask), 4, lr=1e-3)
+    p1 = net.params()
+    want, _, _ = cnn.adam_step(flat.astype(np.float64), g.astype(np.float64), 0.0, 0.0, 1, 1e-3)
+    # the step recomputes the same gradient up to atomic summation order,
+    # which can flip the sign of gradients at rounding level: those entries
+    # only have to move by at most lr
+    big = np.abs(g) > 1e-4 * np.abs(g).max()
+    np.testing.assert_allclose(p1[big], want[big], rtol=0, atol=1e-6 + 1e-6 * np.abs(flat).max())
+    assert np.all(np.abs(p1 - flat) <= 1e-3 * 1.001 + 1e-6)
+    net.close()
+
+
+def test_training_fits_a_fixed_batch():
+    import paper_2607_00348_gb300 as pkg
+    flat, x, tgt, mask, _ = _setup(3, 16)
+    net = pkg.Cnn(16, flat)
+    xd, td, md = _dev(x), _dev(tgt), _dev(mask)
+    first = net.train_step(xd, td, md, 16, lr=2e-3)
+    for _ in range(60):
+        last = net.train_step(xd, td, md, 16, lr=2e-3)
+    # the floor is the targets' own entropy; the fit must close most of the gap
+    ent = float(np.sum(mask * -(tgt * np.log(tgt) + (1 - tgt) * np.log(1 - tgt))) / mask.sum())
+    assert last - ent < 0.3 * (first - ent)
+    net.close()
+
+
+def test_binning_matches_reference():
+    import torch
+    import paper_2607_00348_gb300 as pkg
+    import synth
+    lcs = [synth.short_white(seed=s) for s in (0, 1)] + synth.batch_kepler_like(2, seed=9, n_min=5000,
+                                                                               n_max=9000)
+    net = pkg.Cnn(4)
+    cat = lambda f: _dev(np.concatenate([getattr(lc, f) for lc in lcs]), torch.float64)
+    offs = np.cumsum([0] + [lc.n for lc in lcs])
+    x = torch.empty((len(lcs), cnn.N_BINS), dtype=torch.float32, device=torch.device("cuda:0"))
+    net.bin(cat("t"), cat("y"), cat("dy"), offs, x)
+    got = x.cpu().numpy()
+    for i, lc in enumerate(lcs):
+        want = cnn.bin_flux(lc.t, lc.y, lc.dy)
+        np.testing.assert_allclose(got[i], want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+    net.close()
