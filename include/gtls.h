@@ -339,10 +339,12 @@ gtls_status gtls_cnn_set_params(gtls_cnn* cnn, const float* params);
  * x[i][b] (device, n_lc x 4096 floats) = sum(w r) / sqrt(sum w) over the
  * points of curve i with floor((t - t_min) / (t_max - t_min) * 4096) = b
  * (the last point in bin 4095), r = 1 - y, w = 1/dy^2; 0 for empty bins.
- * Synchronises `stream`.
+ * mean, wsum (device, same shape, nullable): sum(w r) / sum w (0 when
+ * empty) and sum w of every bin.  Synchronises `stream`.
  */
 gtls_status gtls_cnn_bin(gtls_cnn* cnn, const double* t, const double* y, const double* dy,
-                         const int64_t* offsets, int64_t n_lc, float* x, void* stream);
+                         const int64_t* offsets, int64_t n_lc, float* x, float* mean, float* wsum,
+                         void* stream);
 
 /* logits / scores: device [batch][128] floats, each nullable. */
 gtls_status gtls_cnn_forward(gtls_cnn* cnn, const float* x, int32_t batch, float* logits,
@@ -365,7 +367,8 @@ void gtls_cnn_destroy(gtls_cnn* cnn);
 /*
  * Host helpers of the proposal.  Region of a period: floor(128 log(P/0.5) /
  * log(2048)); periods outside [0.5, 1024) belong to none.
- * gtls_region_targets: target[r] = largest sr[i] of region r's periods,
+ * gtls_region_targets: target[r] = largest sr[i] of region r's periods
+ *   (sr: any per-period spectrum; training uses the clipped, scaled SDE),
  *   mask[r] = 1 where region r holds a period (host arrays of 128 floats).
  * gtls_proposal_periods: indices (ascending, into idx of n_periods capacity)
  *   of the periods inside the ceil(frac x regions holding a period) regions

@@ -39,20 +39,23 @@ P_LO, P_HI = 0.5, 1024.0       # days: the regions split [P_LO, P_HI) evenly in 
 # input and targets
 # ---------------------------------------------------------------------------
 
-def bin_flux(t, y, dy, n_bins=N_BINS):
-    """Time-binned deficit SNR: bin b holds the points with
+def bin_sums(t, y, dy, n_bins=N_BINS):
+    """Per-bin sums (sum w r, sum w): bin b holds the points with
     floor((t - t_min) / (t_max - t_min) * n_bins) = b (the last point in the
-    last bin); its value is sum(w r) / sqrt(sum(w)) with r = 1 - y and
-    w = 1/dy^2, i.e. the weighted mean deficit over its standard error;
-    empty bins are 0."""
+    last bin); r = 1 - y, w = 1/dy^2."""
     t = np.asarray(t, np.float64)
     r = 1.0 - np.asarray(y, np.float64)
     w = 1.0 / np.asarray(dy, np.float64) ** 2
     span = t.max() - t.min()
     b = np.floor((t - t.min()) / span * n_bins).astype(np.int64) if span > 0 else np.zeros(t.size, np.int64)
     b = np.clip(b, 0, n_bins - 1)
-    swr = np.bincount(b, weights=w * r, minlength=n_bins)
-    sw = np.bincount(b, weights=w, minlength=n_bins)
+    return np.bincount(b, weights=w * r, minlength=n_bins), np.bincount(b, weights=w, minlength=n_bins)
+
+
+def bin_flux(t, y, dy, n_bins=N_BINS):
+    """Time-binned deficit SNR: sum(w r) / sqrt(sum(w)) per bin (bin_sums),
+    i.e. the weighted mean deficit over its standard error; empty bins are 0."""
+    swr, sw = bin_sums(t, y, dy, n_bins)
     out = np.zeros(n_bins)
     nz = sw > 0
     out[nz] = swr[nz] / np.sqrt(sw[nz])

@@ -335,7 +335,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 // bins 0.  Accumulated in FP64 in shared memory.
 __global__ void __launch_bounds__(1024) k_bin(const double* __restrict__ t, const double* __restrict__ y,
                                               const double* __restrict__ dy, const int64_t* __restrict__ off,
-                                              float* __restrict__ x)
+                                              float* __restrict__ x, float* __restrict__ mean,
+                                              float* __restrict__ wsum)
 {
     extern __shared__ double sb[];   // [kBins] sum w r, [kBins] sum w
     __shared__ double mn[32], mx[32];
@@ -379,6 +380,8 @@ __global__ void __launch_bounds__(1024) k_bin(const double* __restrict__ t, cons
     for (int b = threadIdx.x; b < kBins; b += blockDim.x) {
         const double sw = sb[kBins + b];
         x[(int64_t)lc * kBins + b] = sw > 0.0 ? (float)(sb[b] / sqrt(sw)) : 0.0f;
+        if (mean) mean[(int64_t)lc * kBins + b] = sw > 0.0 ? (float)(sb[b] / sw) : 0.0f;
+        if (wsum) wsum[(int64_t)lc * kBins + b] = (float)sw;
     }
 }
 
@@ -593,7 +596,8 @@ gtls_status gtls_cnn_set_params(gtls_cnn* c, const float* params)
 }
 
 gtls_status gtls_cnn_bin(gtls_cnn* c, const double* t, const double* y, const double* dy,
-                         const int64_t* offsets, int64_t n_lc, float* x, void* stream)
+                         const int64_t* offsets, int64_t n_lc, float* x, float* mean, float* wsum,
+                         void* stream)
 {
     PROP_TRY(check_batch(c, (int)std::min<int64_t>(n_lc, 1 << 30)));
     if (!t || !y || !dy || !offsets || !x) return set_error(GTLS_ERR_INVALID_ARG, "null pointer argument");
@@ -604,7 +608,7 @@ gtls_status gtls_cnn_bin(gtls_cnn* c, const double* t, const double* y, const do
         if (off[i + 1] - off[i] < 1) return set_error(GTLS_ERR_INVALID_ARG, "every light curve needs a point");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PROP_CUDA(cudaMemcpyAsync(c->off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    k_bin<<<(unsigned)n_lc, 1024, 2 * kBins * sizeof(double), st>>>(t + o0, y + o0, dy + o0, c->off, x);
+    k_bin<<<(unsigned)n_lc, 1024, 2 * kBins * sizeof(double), st>>>(t + o0, y + o0, dy + o0, c->off, x, mean, wsum);
     PROP_CUDA(cudaGetLastError());
     PROP_CUDA(cudaStreamSynchronize(st));   // the offsets live in host memory of this call
     return GTLS_OK;

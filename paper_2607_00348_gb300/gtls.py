@@ -142,7 +142,7 @@ SIGNATURES = [
     ("gtls_cnn_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("gtls_cnn_bin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, c_int64_p, ctypes.c_int64, ctypes.c_void_p,
-                                    ctypes.c_void_p]),
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("gtls_cnn_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("gtls_cnn_gradient", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -443,11 +443,11 @@ class Cnn:
             raise ValueError("parameter vector has the wrong size")
         _check(self._lib.gtls_cnn_set_params(self.handle, buf.ctypes.data))
 
-    def bin(self, t, y, dy, offsets, x, stream=None):
+    def bin(self, t, y, dy, offsets, x, mean=None, wsum=None, stream=None):
         offs = np.ascontiguousarray(offsets, np.int64)
         _check(self._lib.gtls_cnn_bin(self.handle, _ptr(t), _ptr(y), _ptr(dy),
                                       offs.ctypes.data_as(c_int64_p), offs.size - 1, _ptr(x),
-                                      _stream_handle(stream)))
+                                      _ptr(mean), _ptr(wsum), _stream_handle(stream)))
 
     def forward(self, x, batch, logits=None, scores=None, stream=None):
         _check(self._lib.gtls_cnn_forward(self.handle, _ptr(x), int(batch), _ptr(logits),

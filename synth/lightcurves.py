@@ -153,7 +153,7 @@ def long_baseline(seed: int = 2, n=144_000, cadence_min=30.0, white_ppm=200.0,
 
 
 def batch_kepler_like(count: int, seed: int = 3, n_min=20_000, n_max=72_000,
-                      inject_fraction=0.3):
+                      inject_fraction=0.3, start: int = 0):
     """Many Kepler-like light curves of uneven length.
 
     Lengths are uniform in [n_min, n_max]; the white-noise level is
@@ -161,10 +161,12 @@ def batch_kepler_like(count: int, seed: int = 3, n_min=20_000, n_max=72_000,
     the curves carries a transit with P log-uniform in [1, 200] d and depth
     log-uniform in [50, 5000] ppm.  The duration follows T14 = 111.6 s^(1/3)
     x P^(1/3) (geometric middle of the 20.05..620.84 s^(2/3) envelope).
+    Curve i of the sequence draws from SeedSequence(seed, spawn_key=(i,));
+    `start` returns curves start .. start + count - 1 of that sequence.
     """
     out = []
-    ss = np.random.SeedSequence(seed)
-    for i, child in enumerate(ss.spawn(count)):
+    for i in range(start, start + count):
+        child = np.random.SeedSequence(seed, spawn_key=(i,))
         rng = np.random.default_rng(child)
         n = int(rng.integers(n_min, n_max + 1))
         sig_ppm = float(math.exp(rng.uniform(math.log(50.0), math.log(2000.0))))

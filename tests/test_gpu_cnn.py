@@ -126,9 +126,15 @@ def test_binning_matches_reference():
     cat = lambda f: _dev(np.concatenate([getattr(lc, f) for lc in lcs]), torch.float64)
     offs = np.cumsum([0] + [lc.n for lc in lcs])
     x = torch.empty((len(lcs), cnn.N_BINS), dtype=torch.float32, device=torch.device("cuda:0"))
-    net.bin(cat("t"), cat("y"), cat("dy"), offs, x)
-    got = x.cpu().numpy()
+    mean = torch.empty_like(x)
+    wsum = torch.empty_like(x)
+    net.bin(cat("t"), cat("y"), cat("dy"), offs, x, mean=mean, wsum=wsum)
+    got, gm, gw = x.cpu().numpy(), mean.cpu().numpy(), wsum.cpu().numpy()
     for i, lc in enumerate(lcs):
         want = cnn.bin_flux(lc.t, lc.y, lc.dy)
         np.testing.assert_allclose(got[i], want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+        swr, sw = cnn.bin_sums(lc.t, lc.y, lc.dy)
+        np.testing.assert_allclose(gw[i], sw, rtol=1e-6)
+        m = np.where(sw > 0, swr / np.where(sw > 0, sw, 1), 0.0)
+        np.testing.assert_allclose(gm[i], m, rtol=1e-6, atol=1e-6 * np.abs(m).max())
     net.close()

@@ -138,3 +138,4 @@ def test_regions_and_targets_by_brute_force():
     top = sorted(valid, key=lambda r: (-scores[r], r))[:k]
     want = [i for i, p in enumerate(periods) if any(edges[r] <= p < edges[r + 1] for r in top)]
     assert list(sel) == want
+

@@ -21,3 +21,10 @@ def test_region_targets_and_proposal_match_the_reference():
         got = pkg.proposal_periods(periods, scores, frac)
         want = cnn.proposed_periods(periods, scores.astype(np.float64), m_or, frac)
         np.testing.assert_array_equal(got, want)
+
+
+def test_library_parameter_layout_matches_the_reference():
+    import paper_2607_00348_gb300 as pkg
+    from paper_2607_00348_gb300 import proposal as pr
+    n = sum(int(np.prod(s)) for _, s in cnn.param_shapes())
+    assert pkg.gtls.load().gtls_cnn_param_count() == n == pr.init_params(0).size
