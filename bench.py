@@ -47,6 +47,11 @@ def _args():
                     help="target CPU time of the oracle sample (cpu_baseline / reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dt0", type=float, default=0.05,
+                    help="T0 step as a fraction of the duration (Eq. N_skip; the paper's sweep uses "
+                         "0.1 and 0.01)")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="periods re-searched with T0 step 1 after the coarse pass (Sect. 2.5)")
     ap.add_argument("--batch-curves", type=int, default=8,
                     help="curves of the uneven-length Kepler-like batch leg (0 = skip it)")
     ap.add_argument("--batch-steps", type=int, default=2)
@@ -68,12 +73,13 @@ def _workload(name):
     return synth.make_workload(name)
 
 
-def _describe(lc, info):
+def _describe(lc, info, dt0=0.05, refine=0):
     cfg = lc.search
     return {
         "workload": f"{lc.name}: {lc.baseline_days:.0f}-day baseline, n={lc.n} points, "
                     f"{info['n_periods']} trial periods {cfg['period_min_days']}-"
-                    f"{cfg['period_max_days']:.0f} d (Ofir, OS=3), dt0=0.05",
+                    f"{cfg['period_max_days']:.0f} d (Ofir, OS=3), dt0={dt0:g}"
+                    + (f", refinement of the {refine} best periods" if refine else ""),
         "n_points": lc.n,
         "n_periods": info["n_periods"],
         "window_point_evaluations": info["wpe"],
@@ -308,7 +314,8 @@ def run_gtls(args):
     plan = pkg.Plan(pkg.PlanConfig(baseline_days=lc.baseline_days, n_points=lc.n,
                                    period_min_days=cfg["period_min_days"],
                                    period_max_days=cfg["period_max_days"],
-                                   periods_per_chunk=args.periods_per_chunk))
+                                   periods_per_chunk=args.periods_per_chunk, dt0=args.dt0,
+                                   refine_periods=args.refine))
     info = {"n_periods": plan.n_periods, "wpe": float(plan.info.wpe),
             "n_windows": int(plan.info.n_windows)}
     t = torch.as_tensor(lc.t, dtype=torch.float64, device=dev)
@@ -411,7 +418,7 @@ def run_gtls(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded numpy generator, Kepler-like)",
-        "config": dict(_describe(lc, info), parallelism=f"replicas x{ws}"),
+        "config": dict(_describe(lc, info, args.dt0, args.refine), parallelism=f"replicas x{ws}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
         "stage_ms": mean_stage, "batched": batched,

@@ -109,6 +109,9 @@ typedef struct {
     int64_t t0_idx;       /* window start in folded order (multiple of the T0 step) */
     int32_t uniform_dy;   /* 1 if all dy were equal (uniform-weight kernel) */
     int32_t refined;      /* number of periods re-searched with T0 step 1 */
+    double snr;           /* sqrt(max(0, chi2_0 - chi2)): the fit's improvement over the
+                             constant model in units of the noise (the paper gives no SNR
+                             formula; for white noise this is the matched-filter SNR) */
 } gtls_result;
 
 /* Optional per-period outputs (device pointers, each nullable, n_periods long). */
@@ -234,7 +237,7 @@ gtls_status gtls_batch_search(gtls_batch* batch, const double* t, const double* 
 
 /*
  * Choose the wave size (the largest, a half, a quarter) and the staged tile
- * size (the plans' own, 40960, 32768 floats) by timing the coarse pass of
+ * size (the plans' own, 49152, 40960, 32768, 24576 floats) by timing the coarse pass of
  * a probe (four runs of 256 periods spread over each of the first four
  * curves that take the tiled kernel) on these inputs; keeps the fastest.
  * Results do not depend on the choice.  Same arguments as

@@ -226,7 +226,10 @@ def full_search(p: OraclePlan, t, y, dy, n_threads=0, refine_top_k=0):
                 dur_points=int(p.dur_pts[j]), duration_days=float(p.q[j] * p.periods[b]),
                 t0_idx=int(r.s_best[b]), t0=float(r.t0[b]), depth=float(r.depth[b]),
                 sde=float(sde[b]), chi2=float(r.chi2[b]), chi2_min=float(r.chi2.min()),
-                chi2_0=r.chi2_0)
+                chi2_0=r.chi2_0,
+                # reading: the paper has no SNR formula; the fit's improvement over
+                # the constant model in noise units (matched-filter SNR for white noise)
+                snr=math.sqrt(max(0.0, r.chi2_0 - float(r.chi2[b]))))
     return r, sr, raw, sde, best
 
 

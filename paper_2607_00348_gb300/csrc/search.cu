@@ -301,6 +301,8 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     const int slot_id = blockIdx.x;
     int lc, p;
     if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
+    unsigned long long* const keys = dk.keys + (int64_t)slot_id * dk.fold_stride;
+    uint32_t* const slotv = dk.slot + (int64_t)slot_id * dk.fold_stride;
     const DevPlan& dp = ds.plans[lc];
     const DevCurve dc = ds.curves[lc];
     const int nb = 1 << dp.bucket_log2;
@@ -316,8 +318,6 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     const uint32_t mul = dp.bucket_mul[p];
     const int ib = dp.idx_bits;
     const unsigned long long idx_mask = (1ull << ib) - 1ull;
-    unsigned long long* keys = dk.keys + (int64_t)slot_id * dk.fold_stride;
-    uint32_t* slotv = dk.slot + (int64_t)slot_id * dk.fold_stride;
     int32_t* sidx = dk.sidx + (int64_t)slot_id * dk.fold_stride;
     float* rs = dk.rs + (int64_t)slot_id * dk.pad_stride;
     float* ws = dk.ws ? dk.ws + (int64_t)slot_id * dk.pad_stride : nullptr;
@@ -385,17 +385,16 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     }
     __syncthreads();
 
-    // 5. inclusive prefix of rfx in folded order: pf[k+1] = sum_{u<=k} rfx
+    // 5. inclusive prefix of rfx in folded order: pf[k+1] = sum_{u<=k} rfx,
+    // one coalesced block-wide scan per blockDim positions
     {
-        const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-        const int64_t k0 = threadIdx.x * per;
-        const int64_t k1 = min(n, k0 + per);
-        long long local = 0;
-        for (int64_t k = k0; k < k1; ++k) local += pf[k + 1];
-        long long run = block_exclusive_scan(local, warp_sums, total);
-        for (int64_t k = k0; k < k1; ++k) {
-            run += pf[k + 1];
-            pf[k + 1] = run;
+        long long carry = 0;
+        for (int64_t base = 0; base < n; base += blockDim.x) {
+            const int64_t k = base + threadIdx.x;
+            const long long v = k < n ? pf[k + 1] : 0;
+            const long long ex = block_exclusive_scan(v, warp_sums, total);
+            if (k < n) pf[k + 1] = carry + ex + v;
+            carry += *total;
         }
         if (threadIdx.x == 0) pf[0] = 0;
     }
@@ -980,6 +979,7 @@ __global__ void __launch_bounds__(1024) k_best(DevSet ds, int lc0, gtls_result* 
         r.t0_idx = dq.t0i[b];
         r.uniform_dy = dc.scal[2] > 0.0 ? 1 : 0;
         r.refined = dp.refine_k;
+        r.snr = sqrt(fmax(0.0, r.chi2_0 - r.chi2));
         *dq.result = r;
         if (results) results[lc] = r;
         if (checks)
@@ -1226,7 +1226,7 @@ gtls_status create_device(gtls_plan* pl)
         const int static_bytes = 8192;  // duration table and reduction scratch, rounded up
         // floats of folded curve staged per tile; the rest of the SM's
         // unified L1/shared memory caches the template tables
-        int want = 49152;
+        int want = 32768;   // measured best on the Kepler-like curve (vs 49152, 40960, 24576, 16384)
         if (const char* e = std::getenv("GTLS_TILE_FLOATS")) want = std::max(4096, std::atoi(e));
         int buf = std::min(want, (smem_optin - static_bytes) / 4) & ~63;
         {
@@ -1631,7 +1631,8 @@ struct gtls_batch {
     int max_kept = 0;
     int fold_smem = 0, topk_smem = 0, median_blocks = 1, n_sm = 0;
     int max_slots = 0;                 // chunk scratch slots allocated
-    int tile_buf_max = 0;              // largest staged tile every tiled curve accepts
+    int tile_buf_max = 0;              // the smallest staged tile of the tiled plans (their own choice)
+    int tile_buf_cap = 0;              // largest staged tile the device's shared memory allows
     gtls::DevChunk dk{};
     gtls::DevSet set{}, set_ref{};
     gtls::DevTiles* d_tiles = nullptr;   // 2 n_lc entries: coarse, refinement
@@ -1977,6 +1978,11 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     b->median_blocks = max_np_blocks;
     b->n_sm = plans[0]->n_sm;
     b->tile_buf_max = any_tiled ? buf_max : 0;
+    {
+        int optin = 0;
+        GTLS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+        b->tile_buf_cap = ((optin - 8192) / 4) & ~63;
+    }
     b->cfg.tile_buf = b->tile_buf_max;
 
     // chunk scratch shared by all curves: slots of the largest curve's strides
@@ -2076,8 +2082,8 @@ gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, cons
     for (int sc : {b->max_slots, b->max_slots / 2, b->max_slots / 4})
         if (sc >= 128 && std::find(slot_c.begin(), slot_c.end(), sc) == slot_c.end()) slot_c.push_back(sc);
     if (slot_c.empty()) slot_c.push_back(b->max_slots);
-    for (int bc : {b->tile_buf_max, 40960, 32768})
-        if (bc <= b->tile_buf_max && bc >= 16384 && std::find(buf_c.begin(), buf_c.end(), bc) == buf_c.end())
+    for (int bc : {b->tile_buf_max, 49152, 40960, 32768, 24576})
+        if (bc <= b->tile_buf_cap && bc >= 16384 && std::find(buf_c.begin(), buf_c.end(), bc) == buf_c.end())
             buf_c.push_back(bc);
     cudaEvent_t e0, e1;
     GTLS_CUDA(cudaEventCreate(&e0));

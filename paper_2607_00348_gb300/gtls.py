@@ -64,7 +64,7 @@ class Result(ctypes.Structure):
                 ("chi2_0", ctypes.c_double), ("period_idx", ctypes.c_int64),
                 ("dur_idx", ctypes.c_int32), ("dur_points", ctypes.c_int32),
                 ("t0_idx", ctypes.c_int64), ("uniform_dy", ctypes.c_int32),
-                ("refined", ctypes.c_int32)]
+                ("refined", ctypes.c_int32), ("snr", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}

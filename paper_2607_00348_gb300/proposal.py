@@ -195,11 +195,13 @@ def scores_for(net, curves, dev):
     return s.cpu().numpy()
 
 
-def proposal_search(net, curves, full_plans, dev, tau, frac=FRAC):
+def proposal_search(net, curves, full_plans, dev, tau, frac=FRAC, verify_sde=None, scores=None):
     """Search every curve on its proposed periods (or its whole grid when
-    the proposal is not confident).  Returns (results, fallback flags,
-    periods searched per curve)."""
-    sc = scores_for(net, curves, dev)
+    the proposal is not confident).  With verify_sde, a curve whose search of
+    the proposed periods ends below that SDE is searched again on its whole
+    grid (the second fallback: the proposal did not hold a detection).
+    Returns (results, fallback flags, periods searched per curve)."""
+    sc = scores_for(net, curves, dev) if scores is None else scores
     chosen, owned, fallback, searched = [], [], [], []
     for i, (c, fp) in enumerate(zip(curves, full_plans)):
         per = fp.periods()
@@ -222,6 +224,17 @@ def proposal_search(net, curves, full_plans, dev, tau, frac=FRAC):
     batch.close()
     for p in owned:
         p.close()
+    if verify_sde is not None:
+        redo = [i for i in range(len(curves)) if not fallback[i] and res[i].sde < verify_sde]
+        if redo:
+            sub = [curves[i] for i in redo]
+            t, y, dy, offs = _pack(sub, dev)
+            batch = _g.Batch([full_plans[i] for i in redo])
+            for i, r in zip(redo, batch.search(t, y, dy, offs)):
+                res[i] = r
+                fallback[i] = True
+                searched[i] += full_plans[i].n_periods
+            batch.close()
     return res, fallback, searched
 
 
@@ -231,10 +244,11 @@ def detected(res, inj, sde_min=9.0, rel=0.01):
     return res.sde >= sde_min and abs(res.period - inj["period"]) / inj["period"] < rel
 
 
-def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None):
+def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verify_sde=None):
     """Recall (SDE >= 9, period within 1 %) and light curves per hour of the
     plain batched search and of the proposal search at every tau, on curves
-    0 .. n_eval-1 of sequence `seed`."""
+    0 .. n_eval-1 of sequence `seed`; per curve, the injection, the plain
+    result and the network's largest region score."""
     import torch
     curves = [c for ch in curve_chunks(seed, n_eval, pool) for c in ch]
     full = [plan_for(c[0].size, c[4]) for c in curves]
@@ -254,11 +268,20 @@ def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None):
            "plain": {"recall": sum(detected(r, i) for r, i in zip(plain, inj)) / max(n_inj, 1),
                      "false_alarms": sum(1 for r, i in zip(plain, inj) if not i and r.sde >= 9.0),
                      "seconds": plain_s, "lc_per_hour": n_eval * 3600.0 / plain_s},
-           "learned": []}
+           "verify_sde": verify_sde, "learned": []}
+    sc = scores_for(net, curves, dev)
+    per_curve = []
+    for i, (c, r) in enumerate(zip(curves, plain)):
+        _, mask = _g.region_targets(full[i].periods(), np.zeros(full[i].n_periods))
+        per_curve.append({"n": int(c[0].size), "inj_period": c[3].get("period"),
+                          "inj_depth": c[3].get("depth"), "plain_period": r.period,
+                          "plain_sde": r.sde, "plain_detected": bool(detected(r, c[3])),
+                          "score_max": float(sc[i][mask > 0].max())})
+    out["per_curve"] = per_curve
     for tau in taus:
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        res, fb, searched = proposal_search(net, curves, full, dev, tau, frac)
+        res, fb, searched = proposal_search(net, curves, full, dev, tau, frac, verify_sde)
         torch.cuda.synchronize()
         s = time.perf_counter() - w0
         row = {"tau": tau, "recall": sum(detected(r, i) for r, i in zip(res, inj)) / max(n_inj, 1),
@@ -300,6 +323,7 @@ def main(argv=None):
     ev.add_argument("--seed", type=int, default=5)
     ev.add_argument("--taus", default="0.0,0.3,0.5")
     ev.add_argument("--frac", type=float, default=FRAC)
+    ev.add_argument("--verify-sde", type=float, default=None)
     ev.add_argument("--json", default=None)
     ev.add_argument("--workers", type=int, default=8)
     a = ap.parse_args(argv)
@@ -328,7 +352,8 @@ def main(argv=None):
         params, meta = load_weights(a.weights)
         net = _g.Cnn(max(a.eval, 1), params)
         taus = [float(v) for v in a.taus.split(",")]
-        out = evaluate(net, a.eval, a.seed, dev, taus, frac=a.frac, pool=pool, log=log)
+        out = evaluate(net, a.eval, a.seed, dev, taus, frac=a.frac, pool=pool, log=log,
+                       verify_sde=a.verify_sde)
         out["weights"] = {k: v for k, v in meta.items() if k != "loss"}
         print(json.dumps(out))
         if a.json:

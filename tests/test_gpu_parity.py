@@ -78,7 +78,28 @@ def test_short_white_full_grid_parity():
     assert res.chi2 == pytest.approx(best_or["chi2"], rel=CHI2_RTOL)
     assert res.depth == pytest.approx(best_or["depth"], rel=1e-6)
     assert res.chi2_0 == pytest.approx(best_or["chi2_0"], rel=1e-12)
+    assert res.snr == pytest.approx(best_or["snr"], abs=1e-2)
     assert res.uniform_dy == 1
+    pl.close()
+
+
+@pytest.mark.parametrize("cfg", [dict(dt0=0.1), dict(dt0=0.01),
+                                 dict(k_min=41.39, k_max=546.94, q_cap=0.112)],
+                         ids=["dt0_0.1", "dt0_0.01", "tls_default_bounds"])
+def test_variants_match_oracle(cfg):
+    # the T0 step sweep of the paper's sensitivity test and TLS's default
+    # duration envelope (Sect. 2.2.2), on the 1440-point curve
+    lc = synth.short_white()
+    c = dict(lc.search, **cfg)
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, c)
+    r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, lc.t, lc.y, lc.dy)
+    pl = gh.plan_for(lc, lc.baseline_days, c)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out)
+    np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
+    assert res.period_idx == best_or["period_idx"]
+    assert (res.dur_idx, res.t0_idx) == (best_or["dur_idx"], best_or["t0_idx"])
     pl.close()
 
 
