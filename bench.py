@@ -146,23 +146,30 @@ class ClockSampler:
 
 
 def _kernel_sha():
+    """Hash of the sources that define the window-search kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_00348_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in ("gtls_internal.h", "search.cu", "window_tiles.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _ncu_traffic(workload):
-    """DRAM bytes per window-search launch from a committed ncu summary, if current."""
-    path = os.path.join(ROOT, "profiles", f"window_search_{workload}.json")
+    """DRAM bytes per window-search launch from the committed ncu summary
+    (profiles/window_tiles_<workload>.md, lines 'kernel_sha: ...' and
+    'dram_bytes_per_launch: ...'), if it was taken on the current kernel."""
+    path = os.path.join(ROOT, "profiles", f"window_tiles_{workload}.md")
+    vals = {}
     try:
-        d = json.load(open(path))
-    except Exception:
+        for line in open(path):
+            for key in ("kernel_sha", "dram_bytes_per_launch"):
+                if line.strip().startswith(key + ":"):
+                    vals[key] = line.split(":", 1)[1].strip().strip("`")
+    except OSError:
         return None
-    if d.get("kernel_sha") != _kernel_sha():
+    if vals.get("kernel_sha") != _kernel_sha() or "dram_bytes_per_launch" not in vals:
         return None
-    return d.get("dram_bytes_per_launch")
+    return float(vals["dram_bytes_per_launch"])
 
 
 def oracle_sample(lc, cpu_seconds):

@@ -56,6 +56,7 @@ namespace {
     } while (0)
 
 constexpr int kFoldThreads = 1024;
+constexpr int kFoldMinBlocks = 1;     // fold CTAs per SM the register budget is sized for
 constexpr int kSearchThreads = 256;
 constexpr int kMedianThreads = 1024;
 constexpr int kMedianCap = 8192;       // values a median block sorts in shared memory
@@ -294,7 +295,7 @@ __global__ void k_curve_reduce(const double* __restrict__ dy, const int64_t* __r
 // fold + sort + gather + prefix sums (one block per period)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kFoldThreads)
+__global__ void __launch_bounds__(kFoldThreads, kFoldMinBlocks)
 k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
 {
     extern __shared__ unsigned char smem[];
