@@ -68,6 +68,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, device=None):
+    """Largest x over the ranks of the default process group (x itself when
+    the job is not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world_size, steps, seconds):
+    """Light curves per hour of the whole job: every rank searched `steps`
+    curves; the job took the slowest rank's time."""
+    return world_size * steps * 3600.0 / seconds
+
+
 def _workload(name):
     import synth
     return synth.make_workload(name)
@@ -98,12 +116,13 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="gtls_clocks_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
@@ -361,12 +380,8 @@ def run_gtls(args):
     clk = clocks.stop()
     plan.set_profiling(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1000.0
-    if ws > 1:
-        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(tt.item())
-    value = ws * args.steps * 3600.0 / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1000.0, dev)
+    value = job_rate(ws, args.steps, total_s)
 
     # end to end: host arrays in pinned memory -> device -> result back
     e2e = None
@@ -381,13 +396,9 @@ def run_gtls(args):
         for k in range(args.steps):
             plan.search_host(th.numpy(), yh.numpy(), dh.numpy(), stream=stream)
         w1 = time.perf_counter()
-        e_s = w1 - w0
-        if ws > 1:
-            tt = torch.tensor([e_s], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e_s = float(tt.item())
+        e_s = max_over_ranks(w1 - w0, dev)
         import ctypes
-        e2e = {"value": ws * args.steps * 3600.0 / e_s, "unit": UNIT,
+        e2e = {"value": job_rate(ws, args.steps, e_s), "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * lc.n,
                "d2h_bytes_per_step": ctypes.sizeof(pkg.Result) + 4}
 

@@ -57,6 +57,9 @@ namespace {
 
 constexpr int kFoldThreads = 1024;
 constexpr int kFoldMinBlocks = 1;     // fold CTAs per SM the register budget is sized for
+constexpr int kFoldUnroll = 4;        // points whose loads a fold thread issues together
+constexpr int kFoldSegKeys = 16384;   // sort keys staged in shared memory per run of buckets
+constexpr int kScanPer = 8;           // consecutive prefix-sum positions per fold thread
 constexpr int kSearchThreads = 256;
 constexpr int kMedianThreads = 1024;
 constexpr int kMedianCap = 8192;       // values a median block sorts in shared memory
@@ -330,11 +333,26 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
 
-    // 1. lattice phase -> bucket, arrival slot inside the bucket
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const long long rho = lattice_rho(dc.d_lat[i], dc.d_f[i], P, inv_p);
-        const uint32_t b = fold_bucket(rho, sh, mul);
-        slotv[i] = in_range(dc.check, 1, b, nb) && in_range(dc.check, 2, rho, P) ? atomicAdd(&hist[b], 1u) : 0u;
+    // 1. lattice phase -> bucket, arrival slot inside the bucket (the loads
+    // of kFoldUnroll points are issued before their arithmetic)
+    const int64_t bs = blockDim.x;
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += kFoldUnroll * bs) {
+        long long dl[kFoldUnroll];
+        float df[kFoldUnroll];
+#pragma unroll
+        for (int u = 0; u < kFoldUnroll; ++u) {
+            const int64_t i = i0 + u * bs;
+            dl[u] = i < n ? dc.d_lat[i] : 0;
+            df[u] = i < n ? dc.d_f[i] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kFoldUnroll; ++u) {
+            const int64_t i = i0 + u * bs;
+            if (i >= n) break;
+            const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
+            const uint32_t b = fold_bucket(rho, sh, mul);
+            slotv[i] = in_range(dc.check, 1, b, nb) && in_range(dc.check, 2, rho, P) ? atomicAdd(&hist[b], 1u) : 0u;
+        }
     }
     __syncthreads();
 
@@ -353,48 +371,101 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     __syncthreads();
 
     // 3. scatter keys (phase << idx_bits | index) into bucket order
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const long long rho = lattice_rho(dc.d_lat[i], dc.d_f[i], P, inv_p);
-        const uint32_t b = fold_bucket(rho, sh, mul);
-        if (!in_range(dc.check, 3, b, nb)) continue;
-        const long long dst = (long long)start[b] + slotv[i];
-        if (in_range(dc.check, 4, dst, n))
-            keys[dst] = ((unsigned long long)rho << ib) | (unsigned long long)i;
-    }
-    __syncthreads();
-
-    // 4. rank inside the bucket -> folded position; gather the folded curve
-    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
-        const unsigned long long key = keys[q];
-        const long long rho = (long long)(key >> ib);
-        const uint32_t b = fold_bucket(rho, sh, mul);
-        if (!in_range(dc.check, 5, b, nb)) continue;
-        const uint32_t lo = start[b], cnt = hist[b];
-        if (!in_range(dc.check, 6, (long long)lo + cnt, n + 1)) continue;
-        uint32_t rank = 0;
-        for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
-        const uint32_t pos = lo + rank;
-        const int32_t idx = (int32_t)(key & idx_mask);
-        if (!in_range(dc.check, 7, pos, n) || !in_range(dc.check, 8, idx, n)) continue;
-        sidx[pos] = idx;
-        rs[pos] = dc.r32[idx];
-        pf[pos + 1] = dc.rfx[idx];
-        if (!uniform) {
-            ws[pos] = dc.w32[idx];
-            wrs[pos] = dc.w32[idx] * dc.r32[idx];
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += kFoldUnroll * bs) {
+        long long dl[kFoldUnroll];
+        float df[kFoldUnroll];
+        uint32_t sl[kFoldUnroll];
+#pragma unroll
+        for (int u = 0; u < kFoldUnroll; ++u) {
+            const int64_t i = i0 + u * bs;
+            dl[u] = i < n ? dc.d_lat[i] : 0;
+            df[u] = i < n ? dc.d_f[i] : 0.0f;
+            sl[u] = i < n ? slotv[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kFoldUnroll; ++u) {
+            const int64_t i = i0 + u * bs;
+            if (i >= n) break;
+            const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
+            const uint32_t b = fold_bucket(rho, sh, mul);
+            if (!in_range(dc.check, 3, b, nb)) continue;
+            const long long dst = (long long)start[b] + sl[u];
+            if (in_range(dc.check, 4, dst, n))
+                keys[dst] = ((unsigned long long)rho << ib) | (unsigned long long)i;
         }
     }
     __syncthreads();
 
-    // 5. inclusive prefix of rfx in folded order: pf[k+1] = sum_{u<=k} rfx,
-    // one coalesced block-wide scan per blockDim positions
+    // 4. rank inside the bucket -> folded position; gather the folded curve.
+    // Runs of whole buckets holding at most kFoldSegKeys keys are staged in
+    // shared memory (one coalesced copy) and ranked there; a single bucket
+    // larger than that (a degenerate phase pile-up) is ranked in global memory.
+    unsigned long long* skeys = reinterpret_cast<unsigned long long*>(total + 1);
+    for (int b_lo = 0; b_lo < nb;) {
+        const uint32_t k0 = start[b_lo];
+        // the largest b_hi in [b_lo + 1, nb] whose keys start[b_lo] .. end(b_hi - 1) fit
+        auto end_of = [&](int b) -> uint32_t { return b < nb ? start[b] : (uint32_t)n; };
+        int b_hi = b_lo + 1;
+        if (end_of(b_hi) - k0 <= (uint32_t)kFoldSegKeys) {
+            int lo = b_hi, hi = nb;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (end_of(mid) - k0 <= (uint32_t)kFoldSegKeys) lo = mid;
+                else hi = mid - 1;
+            }
+            b_hi = lo;
+        }
+        const uint32_t k1 = end_of(b_hi);
+        const bool staged = k1 - k0 <= (uint32_t)kFoldSegKeys;
+        if (staged)
+            for (uint32_t q = threadIdx.x; q < k1 - k0; q += blockDim.x) skeys[q] = keys[k0 + q];
+        __syncthreads();
+        const unsigned long long* kb = staged ? skeys : keys + k0;
+        for (int64_t q = k0 + threadIdx.x; q < k1; q += blockDim.x) {
+            const unsigned long long key = kb[q - k0];
+            const long long rho = (long long)(key >> ib);
+            const uint32_t b = fold_bucket(rho, sh, mul);
+            if (!in_range(dc.check, 5, b - b_lo, b_hi - b_lo)) continue;
+            const uint32_t lo = start[b], cnt = hist[b];
+            if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)k1 + 1)) continue;
+            uint32_t rank = 0;
+            for (uint32_t u = 0; u < cnt; ++u) rank += kb[lo - k0 + u] < key ? 1u : 0u;
+            const uint32_t pos = lo + rank;
+            const int32_t idx = (int32_t)(key & idx_mask);
+            if (!in_range(dc.check, 7, pos, n) || !in_range(dc.check, 8, idx, n)) continue;
+            sidx[pos] = idx;
+            rs[pos] = dc.r32[idx];
+            pf[pos + 1] = dc.rfx[idx];
+            if (!uniform) {
+                ws[pos] = dc.w32[idx];
+                wrs[pos] = dc.w32[idx] * dc.r32[idx];
+            }
+        }
+        __syncthreads();   // the next run overwrites the staged keys
+        b_lo = b_hi;
+    }
+
+    // 5. inclusive prefix of rfx in folded order: pf[k+1] = sum_{u<=k} rfx.
+    // Each thread holds kScanPer consecutive values (loads issued together),
+    // one block-wide scan per blockDim * kScanPer positions.
     {
         long long carry = 0;
-        for (int64_t base = 0; base < n; base += blockDim.x) {
-            const int64_t k = base + threadIdx.x;
-            const long long v = k < n ? pf[k + 1] : 0;
-            const long long ex = block_exclusive_scan(v, warp_sums, total);
-            if (k < n) pf[k + 1] = carry + ex + v;
+        const int64_t span = (int64_t)blockDim.x * kScanPer;
+        for (int64_t base = 0; base < n; base += span) {
+            const int64_t k0 = base + (int64_t)threadIdx.x * kScanPer;
+            long long v[kScanPer];
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) v[u] = k0 + u < n ? pf[k0 + u + 1] : 0;
+            long long run = 0;
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) {
+                run += v[u];
+                v[u] = run;
+            }
+            const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u)
+                if (k0 + u < n) pf[k0 + u + 1] = ex + v[u];
             carry += *total;
         }
         if (threadIdx.x == 0) pf[0] = 0;
@@ -1085,7 +1156,9 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
 
 int fold_smem_bytes(int bucket_log2)
 {
-    return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long);
+    // histogram and starts, scan scratch, staged keys
+    return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long) +
+           kFoldSegKeys * (int)sizeof(unsigned long long);
 }
 
 int topk_smem_bytes(int np, int k)
