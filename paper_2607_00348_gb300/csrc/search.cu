@@ -58,7 +58,8 @@ namespace {
 constexpr int kFoldThreads = 1024;
 constexpr int kFoldMinBlocks = 1;     // fold CTAs per SM the register budget is sized for
 constexpr int kFoldUnroll = 4;        // points whose loads a fold thread issues together
-constexpr int kFoldSegKeys = 16384;   // sort keys staged in shared memory per run of buckets
+constexpr int kFoldSegKeys = 8192;    // sort keys (and folded rfx) staged in shared memory per run of buckets
+constexpr int kRankBatch = 4;         // keys a fold thread ranks before issuing their gathers
 constexpr int kScanPer = 8;           // consecutive prefix-sum positions per fold thread
 constexpr int kSearchThreads = 256;
 constexpr int kMedianThreads = 1024;
@@ -396,14 +397,19 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     }
     __syncthreads();
 
-    // 4. rank inside the bucket -> folded position; gather the folded curve.
-    // Runs of whole buckets holding at most kFoldSegKeys keys are staged in
-    // shared memory (one coalesced copy) and ranked there; a single bucket
-    // larger than that (a degenerate phase pile-up) is ranked in global memory.
-    unsigned long long* skeys = reinterpret_cast<unsigned long long*>(total + 1);
+    // 4. per run of whole buckets: rank inside the bucket -> folded position,
+    // gather the folded curve, and the prefix sums of rfx in folded order
+    // (pf[k+1] = sum_{u<=k} rfx).  A run holds at most kFoldSegKeys keys; its
+    // keys and folded rfx are staged in shared memory, ranked and scanned
+    // there, and pf is written once, coalesced.  A single bucket larger than
+    // that (a phase pile-up) is ranked and scanned in global memory.
+    unsigned long long* const skeys = reinterpret_cast<unsigned long long*>(total + 1);
+    long long* const srfx = reinterpret_cast<long long*>(skeys + kFoldSegKeys);
+    const int64_t span = bs * kScanPer;
+    long long carry = 0;   // sum of rfx over the folded positions before the run
+    if (threadIdx.x == 0) pf[0] = 0;
     for (int b_lo = 0; b_lo < nb;) {
         const uint32_t k0 = start[b_lo];
-        // the largest b_hi in [b_lo + 1, nb] whose keys start[b_lo] .. end(b_hi - 1) fit
         auto end_of = [&](int b) -> uint32_t { return b < nb ? start[b] : (uint32_t)n; };
         int b_hi = b_lo + 1;
         if (end_of(b_hi) - k0 <= (uint32_t)kFoldSegKeys) {
@@ -416,61 +422,108 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
             b_hi = lo;
         }
         const uint32_t k1 = end_of(b_hi);
-        const bool staged = k1 - k0 <= (uint32_t)kFoldSegKeys;
-        if (staged)
-            for (uint32_t q = threadIdx.x; q < k1 - k0; q += blockDim.x) skeys[q] = keys[k0 + q];
-        __syncthreads();
-        const unsigned long long* kb = staged ? skeys : keys + k0;
-        for (int64_t q = k0 + threadIdx.x; q < k1; q += blockDim.x) {
-            const unsigned long long key = kb[q - k0];
-            const long long rho = (long long)(key >> ib);
-            const uint32_t b = fold_bucket(rho, sh, mul);
-            if (!in_range(dc.check, 5, b - b_lo, b_hi - b_lo)) continue;
-            const uint32_t lo = start[b], cnt = hist[b];
-            if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)k1 + 1)) continue;
-            uint32_t rank = 0;
-            for (uint32_t u = 0; u < cnt; ++u) rank += kb[lo - k0 + u] < key ? 1u : 0u;
-            const uint32_t pos = lo + rank;
-            const int32_t idx = (int32_t)(key & idx_mask);
-            if (!in_range(dc.check, 7, pos, n) || !in_range(dc.check, 8, idx, n)) continue;
-            sidx[pos] = idx;
-            rs[pos] = dc.r32[idx];
-            pf[pos + 1] = dc.rfx[idx];
-            if (!uniform) {
-                ws[pos] = dc.w32[idx];
-                wrs[pos] = dc.w32[idx] * dc.r32[idx];
+        const uint32_t len = k1 - k0;
+        if (len <= (uint32_t)kFoldSegKeys) {
+            for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) skeys[q] = keys[k0 + q];
+            __syncthreads();
+            for (uint32_t q0 = threadIdx.x; q0 < len; q0 += kRankBatch * blockDim.x) {
+                uint32_t pos[kRankBatch];
+                int32_t idx[kRankBatch];
+#pragma unroll
+                for (int j = 0; j < kRankBatch; ++j) {
+                    pos[j] = 0xffffffffu;
+                    idx[j] = 0;
+                    const uint32_t q = q0 + j * blockDim.x;
+                    if (q >= len) continue;
+                    const unsigned long long key = skeys[q];
+                    const uint32_t b = fold_bucket((long long)(key >> ib), sh, mul);
+                    if (!in_range(dc.check, 5, (long long)b - b_lo, b_hi - b_lo)) continue;
+                    const uint32_t lo = start[b] - k0, cnt = hist[b];
+                    if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)len + 1)) continue;
+                    uint32_t rank = 0;
+                    for (uint32_t u = 0; u < cnt; ++u) rank += skeys[lo + u] < key ? 1u : 0u;
+                    const int32_t id = (int32_t)(key & idx_mask);
+                    if (!in_range(dc.check, 7, lo + rank, len) || !in_range(dc.check, 8, id, n)) continue;
+                    pos[j] = lo + rank;
+                    idx[j] = id;
+                }
+                float rv[kRankBatch];
+                long long fv[kRankBatch];
+#pragma unroll
+                for (int j = 0; j < kRankBatch; ++j) {
+                    rv[j] = pos[j] != 0xffffffffu ? dc.r32[idx[j]] : 0.0f;
+                    fv[j] = pos[j] != 0xffffffffu ? dc.rfx[idx[j]] : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kRankBatch; ++j) {
+                    if (pos[j] == 0xffffffffu) continue;
+                    const int64_t g = (int64_t)k0 + pos[j];
+                    sidx[g] = idx[j];
+                    rs[g] = rv[j];
+                    srfx[pos[j]] = fv[j];
+                    if (!uniform) {
+                        ws[g] = dc.w32[idx[j]];
+                        wrs[g] = dc.w32[idx[j]] * rv[j];
+                    }
+                }
             }
+            __syncthreads();
+            for (int64_t base = 0; base < len; base += span) {
+                const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
+                long long v[kScanPer];
+                long long run = 0;
+#pragma unroll
+                for (int u = 0; u < kScanPer; ++u) {
+                    run += i0 + u < len ? srfx[i0 + u] : 0;
+                    v[u] = run;
+                }
+                const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
+#pragma unroll
+                for (int u = 0; u < kScanPer; ++u)
+                    if (i0 + u < len) pf[k0 + i0 + u + 1] = ex + v[u];
+                carry += *total;
+            }
+            __syncthreads();   // the next run overwrites the staged keys and rfx
+        } else {
+            for (int64_t q = k0 + threadIdx.x; q < k1; q += blockDim.x) {
+                const unsigned long long key = keys[q];
+                const uint32_t b = fold_bucket((long long)(key >> ib), sh, mul);
+                if (!in_range(dc.check, 5, (long long)b - b_lo, b_hi - b_lo)) continue;
+                const uint32_t lo = start[b], cnt = hist[b];
+                if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)k1 + 1)) continue;
+                uint32_t rank = 0;
+                for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
+                const uint32_t g = lo + rank;
+                const int32_t id = (int32_t)(key & idx_mask);
+                if (!in_range(dc.check, 7, g, n) || !in_range(dc.check, 8, id, n)) continue;
+                sidx[g] = id;
+                rs[g] = dc.r32[id];
+                pf[g + 1] = dc.rfx[id];
+                if (!uniform) {
+                    ws[g] = dc.w32[id];
+                    wrs[g] = dc.w32[id] * dc.r32[id];
+                }
+            }
+            __syncthreads();
+            for (int64_t base = k0; base < k1; base += span) {
+                const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
+                long long v[kScanPer];
+                long long run = 0;
+#pragma unroll
+                for (int u = 0; u < kScanPer; ++u) {
+                    run += i0 + u < k1 ? pf[i0 + u + 1] : 0;
+                    v[u] = run;
+                }
+                const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
+#pragma unroll
+                for (int u = 0; u < kScanPer; ++u)
+                    if (i0 + u < k1) pf[i0 + u + 1] = ex + v[u];
+                carry += *total;
+            }
+            __syncthreads();
         }
-        __syncthreads();   // the next run overwrites the staged keys
         b_lo = b_hi;
     }
-
-    // 5. inclusive prefix of rfx in folded order: pf[k+1] = sum_{u<=k} rfx.
-    // Each thread holds kScanPer consecutive values (loads issued together),
-    // one block-wide scan per blockDim * kScanPer positions.
-    {
-        long long carry = 0;
-        const int64_t span = (int64_t)blockDim.x * kScanPer;
-        for (int64_t base = 0; base < n; base += span) {
-            const int64_t k0 = base + (int64_t)threadIdx.x * kScanPer;
-            long long v[kScanPer];
-#pragma unroll
-            for (int u = 0; u < kScanPer; ++u) v[u] = k0 + u < n ? pf[k0 + u + 1] : 0;
-            long long run = 0;
-#pragma unroll
-            for (int u = 0; u < kScanPer; ++u) {
-                run += v[u];
-                v[u] = run;
-            }
-            const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
-#pragma unroll
-            for (int u = 0; u < kScanPer; ++u)
-                if (k0 + u < n) pf[k0 + u + 1] = ex + v[u];
-            carry += *total;
-        }
-        if (threadIdx.x == 0) pf[0] = 0;
-    }
-    __syncthreads();
 
     // 6. padding: the first D_m folded points repeat after position N-1
     const int64_t dm = dp.dmax_p[p];
@@ -1156,9 +1209,9 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
 
 int fold_smem_bytes(int bucket_log2)
 {
-    // histogram and starts, scan scratch, staged keys
+    // histogram and starts, scan scratch, staged keys and folded rfx
     return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long) +
-           kFoldSegKeys * (int)sizeof(unsigned long long);
+           kFoldSegKeys * (int)(sizeof(unsigned long long) + sizeof(long long));
 }
 
 int topk_smem_bytes(int np, int k)
