@@ -52,6 +52,9 @@ def _args():
                          "0.1 and 0.01)")
     ap.add_argument("--refine", type=int, default=0,
                     help="periods re-searched with T0 step 1 after the coarse pass (Sect. 2.5)")
+    ap.add_argument("--dy-jitter", type=float, default=0.0,
+                    help="multiply every dy by 1 + f * U(-1, 1) (seeded): per-point weights, which "
+                         "the one-thread-per-window kernel searches")
     ap.add_argument("--batch-curves", type=int, default=8,
                     help="curves of the uneven-length Kepler-like batch leg (0 = skip it)")
     ap.add_argument("--batch-steps", type=int, default=2)
@@ -91,13 +94,14 @@ def _workload(name):
     return synth.make_workload(name)
 
 
-def _describe(lc, info, dt0=0.05, refine=0):
+def _describe(lc, info, dt0=0.05, refine=0, jitter=0.0):
     cfg = lc.search
     return {
         "workload": f"{lc.name}: {lc.baseline_days:.0f}-day baseline, n={lc.n} points, "
                     f"{info['n_periods']} trial periods {cfg['period_min_days']}-"
                     f"{cfg['period_max_days']:.0f} d (Ofir, OS=3), dt0={dt0:g}"
-                    + (f", refinement of the {refine} best periods" if refine else ""),
+                    + (f", refinement of the {refine} best periods" if refine else "")
+                    + (f", per-point dy (jitter {jitter:g})" if jitter else ""),
         "n_points": lc.n,
         "n_periods": info["n_periods"],
         "window_point_evaluations": info["wpe"],
@@ -336,6 +340,10 @@ def run_gtls(args):
     pkg.load()
 
     lc = _workload(args.workload)
+    if args.dy_jitter > 0.0:
+        import numpy as np
+        rng = np.random.default_rng(12345)
+        lc.dy = lc.dy * (1.0 + args.dy_jitter * rng.uniform(-1.0, 1.0, lc.n))
     cfg = lc.search
     plan = pkg.Plan(pkg.PlanConfig(baseline_days=lc.baseline_days, n_points=lc.n,
                                    period_min_days=cfg["period_min_days"],
@@ -416,15 +424,18 @@ def run_gtls(args):
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak_tflops = 2.0 * props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     win_s = statistics.mean(win_ms) / 1000.0
-    achieved = 2.0 * info["wpe"] / win_s / 1e12        # 1 FMA per window-point evaluation
+    # 1 FMA per window-point evaluation with uniform dy; 2 (w r s and w s^2)
+    # with per-point dy
+    flop_per_wpe = 2.0 if res.uniform_dy else 4.0
+    achieved = flop_per_wpe * info["wpe"] / win_s / 1e12
     traffic = _ncu_traffic(args.workload)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": "k_window_tiles",
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 FMA "
                               f"lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
-                "achieved_basis": "2 flop x window-point evaluations / mean window-search "
-                                  "stage time (CUDA events on the search stream)"}
+                "achieved_basis": f"{flop_per_wpe:.0f} flop x window-point evaluations / mean "
+                                  "window-search stage time (CUDA events on the search stream)"}
     cpu = None
     if not args.no_cpu_baseline:
         v, threads, desc, _ = oracle_sample(lc, args.cpu_seconds)
@@ -436,7 +447,8 @@ def run_gtls(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded numpy generator, Kepler-like)",
-        "config": dict(_describe(lc, info, args.dt0, args.refine), parallelism=f"replicas x{ws}"),
+        "config": dict(_describe(lc, info, args.dt0, args.refine, args.dy_jitter),
+                       parallelism=f"replicas x{ws}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
         "stage_ms": mean_stage, "batched": batched,

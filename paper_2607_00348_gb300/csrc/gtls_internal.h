@@ -42,6 +42,9 @@ struct DevPlan {
     const int32_t* cfg_nc;      // phase-column lanes per window block per duration
     const int64_t* tmpl2_off;   // offset of duration j in tmpl2 (float2 units)
     const float2* tmpl2;        // template pairs (s_k, s_{k+nc}) of column-pair durations
+    const int64_t* tmplw_off;   // offset of duration j in tmplw (float2 units)
+    const float2* tmplw;        // per-point weights: template pairs (s_k, s_k^2), zero padded
+    const int32_t* cfg_nc_w;    // per-point weights: lanes per window block per duration
     int32_t median_half;        // half width h of the running-median window
     int32_t refine_k;           // periods re-searched with T0 step 1 (0: none)
 };
@@ -96,6 +99,8 @@ struct DevPeriod {
 struct DevTiles {
     int32_t len;              // window starts per tile (L)
     int32_t count;            // tiles per period
+    int32_t len_w;            // the same for per-point weights (tiles of (w r, w) pairs)
+    int32_t count_w;
 };
 
 // Per-light-curve descriptors of a search (device arrays, one entry per
@@ -142,9 +147,12 @@ struct gtls_plan {
     double* in_y = nullptr;
     double* in_dy = nullptr;
     int64_t device_bytes = 0;
-    // tiled window search (uniform weights)
+    // tiled window search (uniform weights; per-point weights: tile_w_*, in
+    // (w r, w) pairs)
     bool tile_ok = false;
     int tile_buf = 0, tile_len = 0, tile_count = 0;
+    bool tile_w_ok = false;
+    int tile_buf_w = 0, tile_len_w = 0, tile_count_w = 0;
     int n_sm = 0;
     unsigned int* tile_counter = nullptr;
     // refinement stage (T0 step 1 on the best periods): plan tables with

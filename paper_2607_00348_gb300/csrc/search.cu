@@ -61,6 +61,7 @@ constexpr int kFoldUnroll = 4;        // points whose loads a fold thread issues
 constexpr int kFoldSegKeys = 8192;    // sort keys (and folded rfx) staged in shared memory per run of buckets
 constexpr int kRankBatch = 4;         // keys a fold thread ranks before issuing their gathers
 constexpr int kScanPer = 8;           // consecutive prefix-sum positions per fold thread
+constexpr int kWeightedTilePairs = 24576;   // (w r, w) pairs staged per tile with per-point weights
 constexpr int kSearchThreads = 256;
 constexpr int kMedianThreads = 1024;
 constexpr int kMedianCap = 8192;       // values a median block sorts in shared memory
@@ -620,7 +621,8 @@ k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(tiles::kThreads, 1)
-k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int buf, unsigned int* counter)
+k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int buf, int weighted,
+               unsigned int* counter)
 {
     using namespace tiles;
     extern __shared__ float tile_smem[];
@@ -637,16 +639,17 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
                 while (g + 1 < sm.nseg && sm.seg[g + 1].item0 <= item) ++g;
                 const int lcg = sm.seg[g].lc;
                 const DevTiles tl = ds.tiles[lcg];
+                const int tcount = weighted ? tl.count_w : tl.count;
                 const int rel = item - sm.seg[g].item0;
-                const int k = rel / tl.count, tau = rel - k * tl.count;
+                const int k = rel / tcount, tau = rel - k * tcount;
                 const int q = sm.seg[g].first + k;
                 int pp = sm.from_list ? ds.outs[lcg].plist[q] : q;
                 if (!in_range(ds.curves[lcg].check, 22, pp, ds.plans[lcg].np)) pp = -1;
                 s_lc = lcg;
                 s_p = pp;
                 s_slot = sm.seg[g].slot0 + k;
-                s_x0 = tau * tl.len;
-                s_len = tl.len;
+                s_x0 = tau * (weighted ? tl.len_w : tl.len);
+                s_len = weighted ? tl.len_w : tl.len;
             }
         }
         __syncthreads();
@@ -663,13 +666,22 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
         const int64_t n = dp.n;
 
         // stage the folded, padded curve [x0, x0 + buf) (zeros past its end)
-        const float* src = dk.rs + (int64_t)slot * dk.pad_stride + x0;
         const int valid = (int)min((int64_t)buf, n + (int64_t)dp.dmax_p[p] + kPadMargin - x0);
-        const int v4 = valid >> 2;
-        for (int i = threadIdx.x; i < v4; i += blockDim.x)
-            reinterpret_cast<float4*>(tile_smem)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
-        for (int i = (v4 << 2) + threadIdx.x; i < buf; i += blockDim.x)
-            tile_smem[i] = i < valid ? src[i] : 0.0f;
+        if (weighted) {
+            // (w r, w) pairs of the folded curve
+            const float* swr = dk.wrs + (int64_t)slot * dk.pad_stride + x0;
+            const float* sw = dk.ws + (int64_t)slot * dk.pad_stride + x0;
+            float2* t2 = reinterpret_cast<float2*>(tile_smem);
+            for (int i = threadIdx.x; i < buf; i += blockDim.x)
+                t2[i] = i < valid ? make_float2(__ldg(swr + i), __ldg(sw + i)) : make_float2(0.0f, 0.0f);
+        } else {
+            const float* src = dk.rs + (int64_t)slot * dk.pad_stride + x0;
+            const int v4 = valid >> 2;
+            for (int i = threadIdx.x; i < v4; i += blockDim.x)
+                reinterpret_cast<float4*>(tile_smem)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
+            for (int i = (v4 << 2) + threadIdx.x; i < buf; i += blockDim.x)
+                tile_smem[i] = i < valid ? src[i] : 0.0f;
+        }
 
         // durations of the period, longest first, with their task ranges
         // (warp 0: one lane per candidate duration, ballot-compacted)
@@ -690,15 +702,15 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
                     t.m_a = (x0 + t.st - 1) / t.st;
                     t.m_b = min(t.m_total, (x0 + tile_len + t.st - 1) / t.st);
                     const int nwin = max(0, t.m_b - t.m_a);
-                    t.variant = dp.cfg_variant[j];
-                    t.nc = dp.cfg_nc[j];
+                    t.variant = weighted ? (int)kWeighted15 : dp.cfg_variant[j];
+                    t.nc = weighted ? dp.cfg_nc_w[j] : dp.cfg_nc[j];
                     t.w = variant_w(t.variant);
                     t.per_task = 32 * t.w / t.nc;
                     t.tasks = (nwin + t.per_task - 1) / t.per_task;
                     const int jrows = (t.d + t.st - 1) / t.st;
                     t.jrows = jrows;
                     t.tg = dp.tmpl + dp.tmpl_off[j];
-                    t.tg2 = dp.tmpl2 + dp.tmpl2_off[j];
+                    t.tg2 = weighted ? dp.tmplw + dp.tmplw_off[j] : dp.tmpl2 + dp.tmpl2_off[j];
                     t.inv_sum_t = dp.inv_sum_t[j] * (1.0f / 1099511627776.0f);  // 2^-40 fixed point
                     t.inv_sum_t_f = dp.inv_sum_t[j];
                     t.sum_t2 = dp.sum_t2[j];
@@ -751,6 +763,7 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
             const DurTask t = dur[k];
             WinCtx c;
             c.tile = tile_smem;
+            c.tile2 = reinterpret_cast<const float2*>(tile_smem);
             c.x0 = x0;
             c.d = t.d;
             c.st = t.st;
@@ -775,6 +788,7 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
             case kCol16: warp_task_colpair<16, 4>(c, lane, best); break;
             case kCol15: warp_task_colpair<15, 5>(c, lane, best); break;
             case kCol12: warp_task_colpair<12, 4>(c, lane, best); break;
+            case kWeighted15: warp_task_weighted<15, 5>(c, lane, best); break;
             default: warp_task_scalar<15, 5>(c, lane, best); break;
             }
         }
@@ -1424,6 +1438,62 @@ gtls_status create_device(gtls_plan* pl)
         if (t2.empty()) t2.assign(1, make_float2(0.0f, 0.0f));
         GTLS_TRY(upload(pl, const_cast<float2**>(&dp.tmpl2), t2));
 
+        // per-point weights: (s_k, s_k^2) pair tables (zero padded like the
+        // templates), lanes per window block, and the tile shape in
+        // (w r, w) pairs
+        {
+            std::vector<int64_t> offw(dp.nd);
+            std::vector<int32_t> ncw(dp.nd, 1);
+            int64_t posw = 0;
+            for (int j = 0; j < dp.nd; ++j) {
+                offw[j] = posw;
+                posw += h.dpts[j] + (tiles::kMaxRing + 2) * (int64_t)h.stride[j] + 64;
+            }
+            std::vector<float2> tw((size_t)std::max<int64_t>(posw, 1), make_float2(0.0f, 0.0f));
+            for (int j = 0; j < dp.nd; ++j) {
+                const float* tj = pl->tmpl_pad.data() + pl->tmpl_pad_off[j];
+                for (int k = 0; k < h.dpts[j]; ++k) tw[(size_t)(offw[j] + k)] = make_float2(tj[k], tj[k] * tj[k]);
+            }
+            GTLS_TRY(upload(pl, const_cast<float2**>(&dp.tmplw), tw));
+            GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmplw_off), offw));
+            const int bufw = std::min(kWeightedTilePairs, (smem_optin - static_bytes) / 8) & ~63;
+            bool fits_w = bufw > 0;
+            for (int j = 0; j < dp.nd; ++j) {
+                const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
+                if ((int64_t)(16 + jrows + 2) * h.stride[j] + 32 > bufw) fits_w = false;
+            }
+            const int64_t len_w = ((int64_t)bufw - h.dmax - 3 * (int64_t)st_max - 96) & ~int64_t(63);
+            pl->tile_w_ok = fits_w && len_w >= 64;
+            if (pl->tile_w_ok) {
+                pl->tile_buf_w = bufw;
+                pl->tile_len_w = (int)len_w;
+                pl->tile_count_w = (int)((n + len_w - 1) / len_w);
+                // lanes per window block: 2^min(v, 4) for st = 2^v odd (distinct banks
+                // across blocks), or 16 / 32 (one block per half-warp / warp: adjacent
+                // columns); the largest column use x task fill wins
+                for (int j = 0; j < dp.nd; ++j) {
+                    const int st = h.stride[j];
+                    int v = 0;
+                    while (v < 4 && ((st >> v) & 1) == 0) ++v;
+                    const int64_t m_total = (n + st - 1) / st;
+                    const int nwin = (int)std::min<int64_t>(m_total, (len_w + st - 1) / st);
+                    double best = -1.0;
+                    for (int nc : {1 << v, 16, 32}) {
+                        const int rounds = (st + nc - 1) / nc;
+                        const double util = (double)st / (double)(nc * rounds);
+                        const int per = 32 * tiles::variant_w(tiles::kWeighted15) / nc;
+                        const int tasks = (nwin + per - 1) / per;
+                        const double fill = (double)nwin / (double)(tasks * per);
+                        if (util * fill > best + 1e-9) {
+                            best = util * fill;
+                            ncw[j] = nc;
+                        }
+                    }
+                }
+            }
+            GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_nc_w), ncw));
+        }
+
         // refinement stage: every duration with T0 step 1 through the (C1, S)
         // variant (one column per lane)
         pl->refine_k = dp.refine_k;
@@ -1473,8 +1543,9 @@ gtls_status create_device(gtls_plan* pl)
         GTLS_TRY(upload(pl, &d_plans, std::vector<DevPlan>{dp, pl->refine_k > 0 ? pl->dp_ref : dp}));
         GTLS_TRY(upload(pl, &d_curves, std::vector<DevCurve>{dc}));
         GTLS_TRY(upload(pl, &d_outs, std::vector<DevPeriod>{pl->dq}));
-        GTLS_TRY(upload(pl, &d_tiles, std::vector<DevTiles>{DevTiles{pl->tile_len, pl->tile_count},
-                                                             DevTiles{pl->tile_len_ref, pl->tile_count_ref}}));
+        GTLS_TRY(upload(pl, &d_tiles,
+                        std::vector<DevTiles>{DevTiles{pl->tile_len, pl->tile_count, pl->tile_len_w, pl->tile_count_w},
+                                              DevTiles{pl->tile_len_ref, pl->tile_count_ref, 0, 0}}));
         pl->set = DevSet{d_plans, d_curves, d_outs, d_tiles};
         pl->set_ref = DevSet{d_plans + 1, d_curves, d_outs, d_tiles + 1};
         GTLS_TRY(upload(pl, &pl->prep_off, std::vector<int64_t>{0, n}));
@@ -1542,6 +1613,7 @@ struct Ctx {
     int n_lc = 1;
     int fold_smem = 0;
     int tile_buf = 0;
+    int tile_buf_w = 0;      // (w r, w) pairs per tile with per-point weights
     int n_sm = 0;
     int median_blocks = 1;   // widest row of the running-median grid
     int topk_smem = 0;
@@ -1558,7 +1630,7 @@ gtls_status stage_mark(Ctx& c, int stage)
 
 // One wave: fold + sort, every window, per-period results.  `counter` must
 // be zero when the window kernel starts (reset here when reset_counter).
-gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, unsigned int* counter,
+gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weighted, unsigned int* counter,
                       bool reset_counter, int64_t max_n, int max_kept)
 {
     const DevSet& ds = ref ? c.set_ref : c.set;
@@ -1567,8 +1639,9 @@ gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, unsigned 
     GTLS_TRY(stage_mark(c, kStageFold));
     if (tiled) {
         if (reset_counter) GTLS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c.st));
-        k_window_tiles<<<c.n_sm, tiles::kThreads, c.tile_buf * (int)sizeof(float), c.st>>>(ds, sm, c.dk,
-                                                                                          c.tile_buf, counter);
+        const int buf = weighted ? c.tile_buf_w : c.tile_buf;
+        const int bytes = buf * (int)(weighted ? sizeof(float2) : sizeof(float));
+        k_window_tiles<<<c.n_sm, tiles::kThreads, bytes, c.st>>>(ds, sm, c.dk, buf, weighted ? 1 : 0, counter);
     } else {
         dim3 grid((unsigned)((max_n + kSearchThreads - 1) / kSearchThreads), (unsigned)max_kept,
                   (unsigned)sm.slots);
@@ -1674,6 +1747,7 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     c.n_lc = 1;
     c.fold_smem = fold_smem_bytes(h.bucket_log2);
     c.tile_buf = pl->tile_buf;
+    c.tile_buf_w = pl->tile_buf_w;
     c.n_sm = pl->n_sm;
     c.median_blocks = (dp.np + median_outs(dp.median_half) - 1) / median_outs(dp.median_half);
     c.topk_smem = topk_smem_bytes(dp.np, pl->refine_k);
@@ -1690,11 +1764,13 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     if (flags & 1u) return fail(GTLS_ERR_INVALID_ARG, "t, y or dy holds a NaN or infinity");
     if (flags & 2u) return fail(GTLS_ERR_INVALID_ARG, "dy must be > 0 everywhere");
 
-    const bool tiled = pl->tile_ok && !(flags & 4u);
+    const bool uniform = !(flags & 4u);
+    const bool tiled = pl->tile_ok && uniform;
+    const bool wtiled = pl->tile_w_ok && !uniform;   // per-point weights, (w r, w) tiles
     for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
         const int cnt = std::min<int>(dk.chunk, dp.np - p0);
-        GTLS_TRY(wave_pass(c, false, single_wave(p0, cnt, pl->tile_count, false), tiled, pl->tile_counter, true,
-                           n, h.max_kept));
+        GTLS_TRY(wave_pass(c, false, single_wave(p0, cnt, wtiled ? pl->tile_count_w : pl->tile_count, false),
+                           tiled || wtiled, wtiled, pl->tile_counter, true, n, h.max_kept));
     }
     GTLS_TRY(sr_sde_pass(c));
     // two-stage T0 search (Sect. 2.5): the refine_k best periods by SDE(P)
@@ -1708,8 +1784,8 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     if (kref > 0) {
         for (int r0 = 0; r0 < kref; r0 += dk.chunk) {
             const int cnt = std::min<int>(dk.chunk, kref - r0);
-            GTLS_TRY(wave_pass(c, true, single_wave(r0, cnt, pl->tile_count_ref, true), tiled, pl->tile_counter,
-                               true, n, h.max_kept));
+            GTLS_TRY(wave_pass(c, true, single_wave(r0, cnt, pl->tile_count_ref, true), tiled, false,
+                               pl->tile_counter, true, n, h.max_kept));
         }
         GTLS_TRY(sr_sde_pass(c));
     }
@@ -1737,6 +1813,7 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
 struct BatchWave {
     SlotMap sm;
     bool tiled;
+    bool weighted;
     bool ref;
     int64_t max_n;
     int max_kept;
@@ -1784,6 +1861,8 @@ struct gtls_batch {
     double tuned_rate = 0.0;           // probe window flop/s of the chosen configuration
     std::vector<gtls::DevTiles> tiles_host;   // 2 n_lc entries
     std::vector<uint8_t> fits, fits_ref;      // curve fits the tiled kernel at cfg.tile_buf
+    std::vector<uint8_t> fits_w;              // ... with per-point weights at tile_buf_w pairs
+    int tile_buf_w = 0;                       // (w r, w) pairs per tile of the weighted waves
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
 };
@@ -1823,12 +1902,18 @@ void batch_release(gtls_batch* b)
 // whose durations do not fit take the one-thread-per-window kernel.
 void batch_tiles(gtls_batch* b, int buf)
 {
-    b->tiles_host.assign(2 * (size_t)b->n_lc, DevTiles{0, 0});
+    b->tiles_host.assign(2 * (size_t)b->n_lc, DevTiles{0, 0, 0, 0});
     b->fits.assign(b->n_lc, 0);
     b->fits_ref.assign(b->n_lc, 0);
+    b->fits_w.assign(b->n_lc, 0);
     for (int i = 0; i < b->n_lc; ++i) {
         const gtls_plan* pl = b->plans[i];
         const PlanHost& h = pl->host;
+        b->fits_w[i] = pl->tile_w_ok && pl->tile_buf_w == b->tile_buf_w ? 1 : 0;
+        if (b->fits_w[i]) {
+            b->tiles_host[i].len_w = pl->tile_len_w;
+            b->tiles_host[i].count_w = pl->tile_count_w;
+        }
         if (!pl->tile_ok) continue;
         int st_max = 1;
         bool fits = true, fits1 = true;
@@ -1842,11 +1927,12 @@ void batch_tiles(gtls_batch* b, int buf)
         const int64_t len1 = ((int64_t)buf - h.dmax - 3 - 96) & ~int64_t(63);
         if (fits && len >= 64) {
             b->fits[i] = 1;
-            b->tiles_host[i] = DevTiles{(int32_t)len, (int32_t)((h.n + len - 1) / len)};
+            b->tiles_host[i].len = (int32_t)len;
+            b->tiles_host[i].count = (int32_t)((h.n + len - 1) / len);
         }
         if (fits1 && len1 >= 64) {
             b->fits_ref[i] = 1;
-            b->tiles_host[b->n_lc + i] = DevTiles{(int32_t)len1, (int32_t)((h.n + len1 - 1) / len1)};
+            b->tiles_host[b->n_lc + i] = DevTiles{(int32_t)len1, (int32_t)((h.n + len1 - 1) / len1), 0, 0};
         }
     }
 }
@@ -1857,21 +1943,23 @@ struct Run {
     int lc, first, count;
 };
 
-void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, bool ref, int wave_slots,
-                 std::vector<BatchWave>& out)
+void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, bool weighted, bool ref,
+                 int wave_slots, std::vector<BatchWave>& out)
 {
     BatchWave w{};
     auto flush = [&]() {
         if (w.sm.slots > 0) out.push_back(w);
         w = BatchWave{};
         w.tiled = tiled;
+        w.weighted = weighted;
         w.ref = ref;
         w.sm.from_list = ref ? 1 : 0;
     };
     flush();
     for (const Run& r : runs) {
         int done = 0;
-        const int tiles_pp = tiled ? b->tiles_host[(ref ? b->n_lc : 0) + r.lc].count : 0;
+        const DevTiles& tl = b->tiles_host[(ref ? b->n_lc : 0) + r.lc];
+        const int tiles_pp = tiled ? (weighted ? tl.count_w : tl.count) : 0;
         const PlanHost& h = b->plans[r.lc]->host;
         while (done < r.count) {
             if (w.sm.slots == wave_slots || w.sm.nseg == kMaxSeg) flush();
@@ -1888,28 +1976,33 @@ void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, 
     flush();
 }
 
-// Per-curve kernel class: 1 = tiled window kernel, 0 = one thread per window.
+// Per-curve kernel class: 1 = tiled window kernel, 2 = tiled with per-point
+// weights, 0 = one thread per window.
 std::vector<uint8_t> batch_classes(const gtls_batch* b, const std::vector<unsigned int>& flags)
 {
     std::vector<uint8_t> c(b->n_lc);
-    for (int i = 0; i < b->n_lc; ++i) c[i] = (b->fits[i] && !(flags[i] & 4u)) ? 1 : 0;
+    for (int i = 0; i < b->n_lc; ++i) {
+        const bool uniform = !(flags[i] & 4u);
+        c[i] = uniform ? (b->fits[i] ? 1 : 0) : (b->fits_w[i] ? 2 : 0);
+    }
     return c;
 }
 
 void batch_waves(const gtls_batch* b, const std::vector<uint8_t>& cls, int wave_slots,
                  std::vector<BatchWave>& coarse, std::vector<BatchWave>& refine)
 {
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool tiled = pass == 0;
+    for (int k = 0; k < 3; ++k) {   // classes 1, 2, 0
+        const int klass = k == 2 ? 0 : k + 1;
         std::vector<Run> runs, runs_ref;
         for (int i = 0; i < b->n_lc; ++i) {
             const gtls_plan* pl = b->plans[i];
-            if ((cls[i] == 1) == tiled) runs.push_back(Run{i, 0, pl->dp.np});
-            const bool tiled_ref = cls[i] == 1 && b->fits_ref[i];
-            if (pl->refine_k > 0 && tiled_ref == tiled) runs_ref.push_back(Run{i, 0, pl->refine_k});
+            if (cls[i] == klass) runs.push_back(Run{i, 0, pl->dp.np});
+            // refinement: tiled only with uniform weights, else one thread per window
+            const int klass_ref = (cls[i] == 1 && b->fits_ref[i]) ? 1 : 0;
+            if (pl->refine_k > 0 && klass_ref == klass) runs_ref.push_back(Run{i, 0, pl->refine_k});
         }
-        build_waves(b, runs, tiled, false, wave_slots, coarse);
-        build_waves(b, runs_ref, tiled, true, wave_slots, refine);
+        build_waves(b, runs, klass != 0, klass == 2, false, wave_slots, coarse);
+        build_waves(b, runs_ref, klass != 0, klass == 2, true, wave_slots, refine);
     }
 }
 
@@ -1922,6 +2015,7 @@ Ctx batch_ctx(const gtls_batch* b, cudaStream_t st)
     c.n_lc = b->n_lc;
     c.fold_smem = b->fold_smem;
     c.tile_buf = b->cfg.tile_buf;
+    c.tile_buf_w = b->tile_buf_w;
     c.n_sm = b->n_sm;
     c.median_blocks = b->median_blocks;
     c.topk_smem = b->topk_smem;
@@ -1953,16 +2047,16 @@ gtls_status batch_enqueue(gtls_batch* b, Ctx& c, const std::vector<BatchWave>& c
     GTLS_CUDA(cudaMemsetAsync(b->counters, 0, std::max(1, tiled_waves) * sizeof(unsigned int), c.st));
     int ci = 0;
     for (const BatchWave& w : coarse)
-        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, b->counters + (w.tiled ? ci++ : 0), false, w.max_n,
-                           w.max_kept));
+        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, w.weighted, b->counters + (w.tiled ? ci++ : 0), false,
+                           w.max_n, w.max_kept));
     GTLS_TRY(sr_sde_pass(c));
     k_topk<<<c.n_lc, 1024, c.topk_smem, c.st>>>(c.set, 0);
     GTLS_CUDA(cudaGetLastError());
     c.launches += 1;
     if (!refine.empty()) {
         for (const BatchWave& w : refine)
-            GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, b->counters + (w.tiled ? ci++ : 0), false, w.max_n,
-                               w.max_kept));
+            GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, w.weighted, b->counters + (w.tiled ? ci++ : 0), false,
+                               w.max_n, w.max_kept));
         GTLS_TRY(sr_sde_pass(c));
     }
     k_best<<<c.n_lc, 1024, 0, c.st>>>(c.set, 0, b->results, b->checks);
@@ -2105,6 +2199,8 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     b->median_blocks = max_np_blocks;
     b->n_sm = plans[0]->n_sm;
     b->tile_buf_max = any_tiled ? buf_max : 0;
+    for (int i = 0; i < b->n_lc && b->tile_buf_w == 0; ++i)
+        if (plans[i]->tile_w_ok) b->tile_buf_w = plans[i]->tile_buf_w;
     {
         int optin = 0;
         GTLS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
@@ -2226,7 +2322,7 @@ gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, cons
         if ((s = batch_upload_tiles(b)) != GTLS_OK) break;
         for (int sc : slot_c) {
             std::vector<BatchWave> waves;
-            build_waves(b, probe, true, false, sc, waves);
+            build_waves(b, probe, true, false, false, sc, waves);
             if ((s = batch_counters(b, (int)waves.size())) != GTLS_OK) break;
             Ctx c = batch_ctx(b, st);
             c.tile_buf = bc;
@@ -2235,7 +2331,7 @@ gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, cons
                 if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = fail(GTLS_ERR_CUDA, "cudaEventRecord");
                 int ci = 0;
                 for (const BatchWave& w : waves) {
-                    s = wave_pass(c, false, w.sm, true, b->counters + ci++, true, w.max_n, w.max_kept);
+                    s = wave_pass(c, false, w.sm, true, false, b->counters + ci++, true, w.max_n, w.max_kept);
                     if (s != GTLS_OK) break;
                 }
             }

@@ -60,6 +60,7 @@ enum Variant : int {
     kCol14 = 7,
     kCol12 = 8,
     kCol8 = 9,
+    kWeighted15 = 10,   // per-point weights: (w r, w) tile pairs x (s_k, s_k^2) template pairs
 };
 
 __host__ __device__ inline int variant_w(int v)
@@ -74,11 +75,12 @@ __host__ __device__ inline int variant_w(int v)
     case kCol15: return 15;
     case kCol14: return 14;
     case kCol12: return 12;
+    case kWeighted15: return 15;
     default: return 8;
     }
 }
 
-__host__ __device__ inline bool variant_colpair(int v) { return v >= kCol16; }
+__host__ __device__ inline bool variant_colpair(int v) { return v >= kCol16 && v <= kCol8; }
 
 struct DurTask {
     int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total, jrows;
@@ -90,6 +92,7 @@ struct DurTask {
 
 struct WinCtx {
     const float* tile;        // shared: folded r at x0 .. x0 + BUF
+    const float2* tile2;      // shared: folded (w r, w) at x0 .. x0 + BUF (per-point weights)
     int x0;
     int d, st, nc, lg_nc, jrows;
     int m_first;              // first window of this warp task
@@ -401,6 +404,98 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
         }
     }
     reduce_pair_finish<W>(c, acc, mb, active, lane, best);
+}
+
+// Per-point weights: every lane ends with (C1w, C2w) = (sum w r s_k,
+// sum w s_k^2) of its windows; S comes from the exact prefix sums and
+// delta-chi2 = delta (delta C2w - 2 C1w) (Eqs. out, in with weights;
+// depth = max(0, S / sum s_k), the unweighted moving average).
+template <int W>
+__device__ __forceinline__ void reduce_weighted_finish(const WinCtx& c, const float2 (&tot)[W], int mb,
+                                                       bool active, int lane, unsigned long long& best)
+{
+    static_assert(W <= 16, "at most 16 windows per block");
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < W ? tot[i] : make_float2(0.0f, 0.0f);
+    const int k = c.lg_nc;
+    int base = 0;
+    if (k >= 1) halve2<16>(v, lane, 1, base);
+    if (k >= 2) halve2<8>(v, lane, 2, base);
+    if (k >= 3) halve2<4>(v, lane, 4, base);
+    if (k >= 4) halve2<2>(v, lane, 8, base);
+    if (k >= 5) {
+        v[0].x += __shfl_xor_sync(0xffffffffu, v[0].x, 16);
+        v[0].y += __shfl_xor_sync(0xffffffffu, v[0].y, 16);
+    }
+    const int cnt = 16 >> min(k, 4);
+    if (!active || (k >= 5 && (lane & 16))) return;
+    float2 e[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) e[i] = v[i];
+    for (int i = 0; i < cnt; ++i) {
+        const int w = base + i;
+        const long long m = mb + w;
+        if (w < W && m < c.m_total) {
+            const long long s0 = m * c.st;
+            const long long sfx = c.pf[s0 + c.d] - c.pf[s0];
+            const float depth = fmaxf(0.0f, fixed_to_float(sfx) * c.inv_sum_t);
+            const float dchi = depth * fmaf(depth, e[i].y, -2.0f * e[i].x);
+            unsigned int u = __float_as_uint(dchi);
+            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            const unsigned long long key =
+                ((unsigned long long)u << 32) | ((unsigned long long)c.j << 24) | (unsigned long long)m;
+            best = key < best ? key : best;
+        }
+    }
+}
+
+// Per-point weights: nc lanes per window block (2^v for st = 2^v odd, or 16 /
+// 32: one block per half-warp / warp), each lane one column at a time; each
+// FFMA2 multiplies the staged pair (w r, w) of a point by the template pair
+// (s_k, s_k^2), i.e. one FFMA2 per window-point evaluation.  Pairs are 8-byte
+// shared loads: the 16 lanes of a half-warp read 16 distinct bank pairs.
+template <int W, int R>
+__device__ void warp_task_weighted(const WinCtx& c, int lane, unsigned long long& best)
+{
+    static_assert(W % R == 0, "ring length must divide the unroll period");
+    const int b = lane >> c.lg_nc;
+    const int cl = lane & (c.nc - 1);
+    bool active;
+    const int mb = block_start(c, b, W, active);
+    const int st = c.st, jrows = c.jrows;
+    float2 acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = make_float2(0.0f, 0.0f);
+    if (active) {
+        const float2* abase = c.tile2 + (mb * st - c.x0);
+        for (int rho = cl; rho < st; rho += c.nc) {
+            const float2* a = abase + rho;
+            const float2* tp = c.tg2 + rho;
+            float2 ring[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
+            tp += R * st;
+            float2 p[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) p[w] = a[w * st];
+            const float2* an = a + W * st;
+            for (int jj = 0; jj < jrows; jj += W) {
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    if (jj + u >= jrows) break;
+                    const float2 tcur = ring[u % R];
+                    ring[u % R] = __ldg(tp);
+                    tp += st;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+                    p[u] = *an;
+                    an += st;
+                }
+            }
+        }
+    }
+    reduce_weighted_finish<W>(c, acc, mb, active, lane, best);
 }
 
 }  // namespace tiles

@@ -278,3 +278,24 @@ def test_long_baseline_full_size_sampled_parity():
     assert np.all(sr > 0) and np.all(sr <= 1.0)
     assert abs(out["sde_raw"].mean()) < 1e-9
     pl.close()
+
+
+def test_kepler_like_per_point_weights_sampled_parity():
+    # per-point dy (tiled (w r, w) kernel) at full size, sampled periods
+    lc = synth.kepler_like()
+    rng = np.random.default_rng(12345)
+    dy = lc.dy * (1.0 + 0.3 * rng.uniform(-1.0, 1.0, lc.n))
+    cfg = lc.search
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, dy)
+    assert res.uniform_dy == 0
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    npd = op.periods.size
+    near = int(np.argmin(np.abs(op.periods - lc.injected["period"])))
+    sel = np.unique(np.concatenate([np.arange(0, npd, 10000), np.arange(near - 3, near + 4),
+                                    [npd - 1]]))
+    r_or = osr.search_periods(op, lc.t, lc.y, dy, sel)
+    np.testing.assert_allclose(out["chi2"][sel], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, lc.t, lc.y, dy, r_or, out, sel)
+    assert abs(res.period - 37.0) / 37.0 < 2e-3
+    pl.close()
