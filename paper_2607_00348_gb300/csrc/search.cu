@@ -620,7 +620,7 @@ k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
 // tiled window search (uniform weights): see window_tiles.cuh
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(tiles::kThreads, 1)
+__global__ void __launch_bounds__(tiles::kThreads, tiles::kCtasPerSm)
 k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int buf, int weighted,
                unsigned int* counter)
 {
@@ -1641,7 +1641,8 @@ gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weig
         if (reset_counter) GTLS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c.st));
         const int buf = weighted ? c.tile_buf_w : c.tile_buf;
         const int bytes = buf * (int)(weighted ? sizeof(float2) : sizeof(float));
-        k_window_tiles<<<c.n_sm, tiles::kThreads, bytes, c.st>>>(ds, sm, c.dk, buf, weighted ? 1 : 0, counter);
+        k_window_tiles<<<c.n_sm * tiles::kCtasPerSm, tiles::kThreads, bytes, c.st>>>(ds, sm, c.dk, buf,
+                                                                                   weighted ? 1 : 0, counter);
     } else {
         dim3 grid((unsigned)((max_n + kSearchThreads - 1) / kSearchThreads), (unsigned)max_kept,
                   (unsigned)sm.slots);

@@ -45,6 +45,7 @@ namespace tiles {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kCtasPerSm = 1;  // persistent window CTAs per SM (each with its own staged tile)
 constexpr int kMaxDur = 64;
 constexpr int kMaxRing = 7;   // template rows fetched ahead; tables carry (kMaxRing + 2) st + 64 zeros
 
