@@ -308,6 +308,7 @@ def batch_leg(args, dev, stream):
     same = all(a.as_dict() == b.as_dict() for a, b in zip(res_b, res_s))
     info = batch.info()
     n = len(lcs)
+    learned = learned_leg(args, lcs, plans, res_b, dev)
     out = {"value": n * 3600e3 / ms_b, "unit": UNIT, "curves": n,
            "plain_value": n * 3600e3 / ms_s, "ms_per_step": ms_b, "plain_ms_per_step": ms_s,
            "identical_results": same, "points": int(offs[-1]),
@@ -316,11 +317,44 @@ def batch_leg(args, dev, stream):
            "tile_floats": int(info.tile_floats), "graph_kernels": int(info.graph_kernels),
            "gpu_launches_per_step": int(info.last_launches),
            "workload": f"first {n} curves of the uneven-length Kepler-like batch (seed 3, "
-                       "20k-72k points, 50-2000 ppm, 30 % injected)"}
+                       "20k-72k points, 50-2000 ppm, 30 % injected)",
+           "learned": learned}
     batch.close()
     for p in plans:
         p.close()
     return out
+
+
+def learned_leg(args, lcs, plans, plain, dev):
+    """The learned period proposal on the same curves: network scores of the
+    binned curves, a search of the proposed periods when the best score
+    reaches tau, the whole grid otherwise or when that search ends below
+    SDE 9 (wall clock of the whole pipeline, host steps included).
+    Detections: SDE >= 9 (and, for injected curves, the period within 1 %)."""
+    import torch
+
+    import paper_2607_00348_gb300 as pkg
+    from paper_2607_00348_gb300 import proposal as pr
+    if not os.path.exists(pr.WEIGHTS):
+        return None
+    params, meta = pr.load_weights()
+    net = pkg.Cnn(len(lcs), params)
+    curves = [(lc.t, lc.y, lc.dy, dict(lc.injected), float(lc.baseline_days)) for lc in lcs]
+    tau, frac = 0.35, pr.FRAC
+    pr.proposal_search(net, curves, plans, dev, tau, frac, verify_sde=9.0)   # warm-up
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    res, fb, searched = pr.proposal_search(net, curves, plans, dev, tau, frac, verify_sde=9.0)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - w0
+    net.close()
+    det = lambda r, c: r.sde >= 9.0 and (not c[3] or abs(r.period - c[3]["period"]) / c[3]["period"] < 0.01)
+    return {"value": len(lcs) * 3600.0 / sec, "unit": UNIT, "tau": tau, "frac": frac,
+            "verify_sde": 9.0, "fallbacks": int(sum(fb)), "periods_searched": int(sum(searched)),
+            "periods_total": int(sum(p.n_periods for p in plans)),
+            "detections_plain": int(sum(det(r, c) for r, c in zip(plain, curves))),
+            "detections_learned": int(sum(det(r, c) for r, c in zip(res, curves))),
+            "weights": f"{meta['train_curves']} training curves (seed {meta['seed']})"}
 
 
 def run_gtls(args):
