@@ -169,11 +169,16 @@ class ClockSampler:
 
 
 def _kernel_sha():
-    """Hash of the sources that define the window-search kernel."""
+    """Hash of the code (comments and blank space removed) of the sources
+    that define the window-search kernel."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_00348_gb300", "csrc")
     for f in ("gtls_internal.h", "search.cu", "window_tiles.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        src = open(os.path.join(csrc, f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,17 +1,25 @@
 // libgtls: the TLS period-grid search on one GPU (sm_103a).
 //
-// Pipeline of one search (all on `stream`):
-//   k_curve_minmax, k_curve_prep, k_curve_reduce   per-point derived arrays, chi2_0
-//   for every chunk of periods:
+// Pipeline of one search (all on `stream`; a batch runs the same kernels over
+// many curves, see gtls_batch below):
+//   k_curve_reset, k_curve_minmax, k_curve_prep, k_curve_reduce
+//                      per-point derived arrays, chi2_0, input checks
+//   for every wave (chunk) of periods:
 //     k_fold_sort      fold on the exact phase lattice (Eq. phase), bucket
 //                      sort by (phase, index), gather the folded curve, pad it
 //                      with its first D_m points (Sect. 2.3.2) and build the
 //                      exact prefix sums that give every moving average
 //                      (Eq. cumsum)
-//     k_window_search  every duration and T0 start: depth (Eqs. k, depth),
-//                      chi2 - chi2_0 (Eqs. out, in), per-period minimum
+//     k_window_tiles   every duration and T0 start (Eq. N_skip): depth
+//                      (Eqs. k, depth), chi2 - chi2_0 (Eqs. out, in),
+//                      per-period minimum; staged tiles, window_tiles.cuh
+//                      (k_window_search: one thread per window, for plans
+//                      whose durations do not fit a tile)
 //     k_period_finalize chi2(P), depth, T0 of each period's minimum
-//   k_sr_stats, k_median_sde, k_best     SR, SDE_raw, SDE, argmax (Sect. 2.4)
+//   k_sr_stats_set, k_median_sde_set        SR, SDE_raw, SDE (Sect. 2.4)
+//   k_topk + waves with T0 step 1           refinement of the best periods
+//                                           (Sect. 2.5), then SR/SDE again
+//   k_best                                  the candidate of largest SDE
 #include <cuda_runtime.h>
 
 #include <algorithm>
