@@ -299,3 +299,35 @@ def test_kepler_like_per_point_weights_sampled_parity():
     _check_argmins(op, lc.t, lc.y, dy, r_or, out, sel)
     assert abs(res.period - 37.0) / 37.0 < 2e-3
     pl.close()
+
+
+def test_phase_pile_up_takes_the_global_memory_fold():
+    # 20,000 points one day apart: at trial periods of 0.5, 1 and 2 days every
+    # point shares one or two phases, so single buckets hold 10,000-20,000
+    # keys (beyond one shared-memory run); other periods spread them
+    n = 20000
+    t = np.arange(n, dtype=np.float64)
+    rng = np.random.default_rng(4)
+    y = 1.0 + rng.normal(0, 1e-3, n)
+    dy = np.full(n, 1e-3)
+    periods = np.array([0.5, 1.0, 2.0, 3.0, 0.77123, 1.5, 7.3])
+    base = float(t[-1] - t[0])
+    op = gh.oracle_plan_for(n, base, periods_days=periods)
+    r_or = osr.search_periods(op, t, y, dy)
+    pl = gh.plan_for(n, base, periods_days=periods)
+    res, out = gh.gpu_search(pl, t, y, dy)
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, t, y, dy, r_or, out)
+    pl.close()
+
+
+def test_flat_light_curve():
+    # y == 1 exactly: chi2_0 = 0, every window fits depth 0, SR = 0/0 := 1, SDE = 0
+    lc = synth.short_white()
+    y = np.ones(lc.n)
+    pl = gh.plan_for(lc, lc.baseline_days, lc.search)
+    res, out = gh.gpu_search(pl, lc.t, y, lc.dy)
+    assert res.chi2_0 == 0.0 and np.all(out["chi2"] == 0.0)
+    assert np.all(out["depth"] == 0.0) and np.all(out["sr"] == 1.0) and np.all(out["sde"] == 0.0)
+    assert res.snr == 0.0
+    pl.close()
