@@ -125,3 +125,35 @@ def test_batch_reports_the_bad_curve_and_stays_usable():
         pkg.Batch([plans[0], plans[0]])
     for p in plans:
         p.close()
+
+
+def test_weighted_refinement_and_graph_recapture():
+    import paper_2607_00348_gb300 as pkg
+    # per-point dy with the refinement stage: single search against the oracle
+    lc = synth.short_white(seed=3)
+    rng = np.random.default_rng(8)
+    dyw = lc.dy * (1.0 + 0.25 * rng.uniform(-1.0, 1.0, lc.n))
+    cfg = dict(lc.search, refine_periods=40)
+    op = gh.oracle_plan_for(lc.n, lc.baseline_days, cfg)
+    r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, lc.t, lc.y, dyw, refine_top_k=40)
+    pl = gh.plan_for(lc, lc.baseline_days, cfg)
+    res, out = gh.gpu_search(pl, lc.t, lc.y, dyw)
+    assert res.uniform_dy == 0 and res.refined == 40
+    assert np.array_equal(out["refined"].astype(bool), r_or.refined)
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=1e-5, atol=0)
+    np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=1e-3)
+    assert res.period_idx == best_or["period_idx"]
+    # the same plans in a batch whose dy switches between uniform and per-point
+    # from call to call (the captured graph is recaptured for each class set)
+    other = synth.short_white(seed=6)
+    pl2 = gh.plan_for(other, other.baseline_days, other.search)
+    batch = pkg.Batch([pl, pl2], wave_slots=500)
+    for dy0 in (dyw, lc.dy, dyw):
+        curves = [(lc.t, lc.y, dy0, {}), (other.t, other.y, other.dy, {})]
+        singles = [gh.gpu_search(pl, lc.t, lc.y, dy0), gh.gpu_search(pl2, other.t, other.y, other.dy)]
+        t, y, dy, offs = _packed(curves)
+        res_b = batch.search(t, y, dy, offs)
+        _same(batch, [pl, pl2], res_b, singles)
+    batch.close()
+    pl.close()
+    pl2.close()
