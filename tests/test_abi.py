@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2607_00348_gb300 as pkg
@@ -96,3 +97,29 @@ def test_ctypes_structs_match_the_header_layout():
             binding.PlanInfo.wpe.offset, ctypes.sizeof(binding.BatchInfo),
             binding.BatchInfo.last_launches.offset, binding.BatchInfo.tuned_flops.offset]
     assert got == want
+
+
+def test_batch_and_network_reject_invalid_arguments_before_device_work():
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    # a batch needs 1 .. 65535 curves and a non-null plan array
+    assert lib.gtls_batch_create(None, 1, 0, ctypes.byref(h)) == 1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.gtls_batch_create(arr, 0, 0, ctypes.byref(h)) == 1
+    assert lib.gtls_batch_create(arr, 1, -1, ctypes.byref(h)) == 1
+    assert not h.value
+    # the proposal network: batch size range, null outputs
+    assert lib.gtls_cnn_create(0, None, ctypes.byref(h)) == 1
+    assert lib.gtls_cnn_create(5000, None, ctypes.byref(h)) == 1
+    assert lib.gtls_cnn_create(4, None, None) == 1
+    assert not h.value
+    # the host helpers of the proposal
+    per = np.array([1.0, 2.0, 3.0])
+    idx = np.zeros(3, np.int64)
+    n = ctypes.c_int64(0)
+    sc = np.zeros(128, np.float32)
+    assert lib.gtls_proposal_periods(per.ctypes.data_as(binding.c_double_p), 3, sc.ctypes.data, 0.0,
+                                     idx.ctypes.data_as(binding.c_int64_p), ctypes.byref(n)) == 1
+    assert lib.gtls_proposal_periods(per.ctypes.data_as(binding.c_double_p), 3, sc.ctypes.data, 1.5,
+                                     idx.ctypes.data_as(binding.c_int64_p), ctypes.byref(n)) == 1
+    assert lib.gtls_region_targets(None, None, 3, None, None) == 1
