@@ -1015,58 +1015,79 @@ __global__ void __launch_bounds__(kMedianThreads) k_median_sde_set(DevSet ds, in
 }
 
 // Curve lc0 + blockIdx.x: clears its refined flags, then takes the
-// refine_k periods with the largest SDE (ties: lower index first), in rank
-// order, into its plist and flags them.  k argmax passes over the periods
-// not yet taken (a bit mask in shared memory).
+// refine_k periods with the largest SDE (ties: lower index first) into its
+// plist in ascending period order and flags them.  A radix select over the
+// order-preserving 64-bit keys of SDE (eight passes of 8-bit histograms)
+// finds the key T of the k-th largest; every key above T is taken, and of
+// the keys equal to T the lowest indices (a block-wide scan in index order).
 __global__ void __launch_bounds__(1024) k_topk(DevSet ds, int lc0)
 {
-    extern __shared__ unsigned int taken[];
-    __shared__ double bv[1024];
-    __shared__ int bi[1024];
+    __shared__ unsigned int hist[256];
+    __shared__ long long warp_sums[33];
+    __shared__ unsigned long long s_prefix, s_mask;
+    __shared__ long long s_need;
     const int lc = lc0 + blockIdx.x;
     const int np = ds.plans[lc].np, k = ds.plans[lc].refine_k;
     const DevPeriod dq = ds.outs[lc];
     for (int i = threadIdx.x; i < np; i += blockDim.x) dq.refined[i] = 0;
     if (k <= 0) return;
-    const int words = (np + 31) >> 5;
-    for (int w = threadIdx.x; w < words; w += blockDim.x) taken[w] = 0u;
+    if (threadIdx.x == 0) {
+        s_prefix = 0ull;
+        s_mask = 0ull;
+        s_need = k;
+    }
     __syncthreads();
-    for (int r = 0; r < k; ++r) {
-        double v = -INFINITY;
-        int idx = 0x7fffffff;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix, mask = s_mask;
         for (int i = threadIdx.x; i < np; i += blockDim.x) {
-            if (taken[i >> 5] & (1u << (i & 31))) continue;
-            const double x = dq.sde[i];
-            if (x > v || (x == v && i < idx)) {
-                v = x;
-                idx = i;
-            }
+            const unsigned long long u = double_order_key(dq.sde[i]);
+            if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
         }
-        bv[threadIdx.x] = v;
-        bi[threadIdx.x] = idx;
         __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                const double ov = bv[threadIdx.x + s];
-                const int oi = bi[threadIdx.x + s];
-                if (ov > bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-                    bv[threadIdx.x] = ov;
-                    bi[threadIdx.x] = oi;
-                }
-            }
-            __syncthreads();
-        }
         if (threadIdx.x == 0) {
-            const int b = bi[0];
-            if (in_range(dq.check, 21, b, np)) {
-                dq.plist[r] = b;
-                taken[b >> 5] |= 1u << (b & 31);
-                dq.refined[b] = 1;
-            } else {
-                dq.plist[r] = 0;
+            long long above = 0;
+            int b = 255;
+            for (; b > 0; --b) {
+                if (above + hist[b] >= s_need) break;
+                above += hist[b];
             }
+            s_need -= above;
+            s_prefix = prefix | ((unsigned long long)b << shift);
+            s_mask = mask | (255ull << shift);
         }
         __syncthreads();
+    }
+    const unsigned long long thr = s_prefix;
+    const long long need_eq = s_need;   // keys equal to thr to take, lowest indices first
+    // selection in index order: contiguous chunk per thread, two block scans
+    long long* total = warp_sums + 32;
+    const int chunk = (np + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = threadIdx.x * chunk, i1 = min(np, i0 + chunk);
+    long long gt = 0, eq = 0;
+    for (int i = i0; i < i1; ++i) {
+        const unsigned long long u = double_order_key(dq.sde[i]);
+        gt += u > thr ? 1 : 0;
+        eq += u == thr ? 1 : 0;
+    }
+    const long long gt_before = block_exclusive_scan(gt, warp_sums, total);
+    const long long eq_before = block_exclusive_scan(eq, warp_sums, total);
+    long long pos = gt_before + min(eq_before, need_eq);
+    long long eq_seen = eq_before;
+    for (int i = i0; i < i1; ++i) {
+        const unsigned long long u = double_order_key(dq.sde[i]);
+        bool take = u > thr;
+        if (u == thr) {
+            take = eq_seen < need_eq;
+            ++eq_seen;
+        }
+        if (!take) continue;
+        if (in_range(dq.check, 21, pos, k)) {
+            dq.plist[pos] = i;
+            dq.refined[i] = 1;
+        }
+        ++pos;
     }
 }
 
@@ -1236,9 +1257,9 @@ int fold_smem_bytes(int bucket_log2)
            kFoldSegKeys * (int)(sizeof(unsigned long long) + sizeof(long long));
 }
 
-int topk_smem_bytes(int np, int k)
+int topk_smem_bytes(int, int)
 {
-    return k > 0 ? ((np + 31) / 32) * (int)sizeof(unsigned int) : 0;
+    return 0;   // the selection uses static shared memory only
 }
 
 constexpr int kMedianSmem = kMedianCap * (int)(sizeof(double) + sizeof(int));
@@ -1536,8 +1557,6 @@ gtls_status create_device(gtls_plan* pl)
                 pl->tile_len_ref = (int)len1;
                 pl->tile_count_ref = (int)((n + len1 - 1) / len1);
             }
-            if (topk_smem_bytes(dp.np, pl->refine_k) > 200 * 1024)
-                return fail(GTLS_ERR_INVALID_ARG, "too many periods for the refinement selection");
         }
         GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
     }
