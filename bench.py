@@ -169,16 +169,24 @@ class ClockSampler:
 
 
 def _kernel_sha():
-    """Hash of the code (comments and blank space removed) of the sources
-    that define the window-search kernel."""
+    """Hash of the window-search kernel's code (comments and blank space
+    removed): the k_window_tiles function, its warp tasks and the shared
+    device structures."""
     import re
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2607_00348_gb300", "csrc")
-    for f in ("gtls_internal.h", "search.cu", "window_tiles.cuh"):
-        src = open(os.path.join(csrc, f)).read()
+
+    def code(src):
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
-        h.update(" ".join(src.split()).encode())
+        return " ".join(src.split())
+
+    csrc = os.path.join(ROOT, "paper_2607_00348_gb300", "csrc")
+    search = open(os.path.join(csrc, "search.cu")).read()
+    start = search.index("k_window_tiles(DevSet")
+    body = search[start:search.index("\n}\n", start) + 3]
+    h = hashlib.sha256()
+    for part in (open(os.path.join(csrc, "gtls_internal.h")).read(),
+                 open(os.path.join(csrc, "window_tiles.cuh")).read(), body):
+        h.update(code(part).encode())
     return h.hexdigest()[:16]
 
 
