@@ -153,6 +153,10 @@ struct gtls_plan {
     int tile_buf = 0, tile_len = 0, tile_count = 0;
     bool tile_w_ok = false;
     int tile_buf_w = 0, tile_len_w = 0, tile_count_w = 0;
+    // durations too long for a tile (marked kWindowOnly): searched by the
+    // one-thread-per-window kernel in the same waves
+    bool has_window_only = false, has_window_only_ref = false;
+    std::vector<int32_t> variant_host;   // window-kernel variant per duration (host copy)
     int n_sm = 0;
     unsigned int* tile_counter = nullptr;
     // refinement stage (T0 step 1 on the best periods): plan tables with

@@ -564,7 +564,7 @@ __device__ __forceinline__ int kept_j(const DevPlan& dp, int p, int slot)
 }
 
 __global__ void __launch_bounds__(kSearchThreads)
-k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
+k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int only_window_only)
 {
     __shared__ unsigned long long red[kSearchThreads / 32];
     const int slot_id = blockIdx.z;
@@ -574,6 +574,7 @@ k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     const DevCurve dc = ds.curves[lc];
     const int j = kept_j(dp, p, blockIdx.y);
     if (j < 0) return;
+    if (only_window_only && dp.cfg_variant[j] != tiles::kWindowOnly) return;
     const int d = dp.dpts[j], st = dp.stride[j];
     const int64_t n = dp.n;
     const int64_t nwin = (n + st - 1) / st;
@@ -714,7 +715,7 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
                     t.nc = weighted ? dp.cfg_nc_w[j] : dp.cfg_nc[j];
                     t.w = variant_w(t.variant);
                     t.per_task = 32 * t.w / t.nc;
-                    t.tasks = (nwin + t.per_task - 1) / t.per_task;
+                    t.tasks = (!weighted && t.variant == kWindowOnly) ? 0 : (nwin + t.per_task - 1) / t.per_task;
                     const int jrows = (t.d + t.st - 1) / t.st;
                     t.jrows = jrows;
                     t.tg = dp.tmpl + dp.tmpl_off[j];
@@ -1412,15 +1413,22 @@ gtls_status create_device(gtls_plan* pl)
             need = std::max<int64_t>(need, need_len + h.dmax + 3 * (int64_t)st_mx + 96 + 63);
             buf = std::max(buf, std::min((int)((need + 63) & ~63), (smem_optin - static_bytes) / 4 & ~63));
         }
-        int st_max = 1;
-        bool fits = buf > 0;
+        // durations whose register block of rows and a 64-window tile fit the
+        // staged buffer take the tiled kernel; longer ones are marked for the
+        // one-thread-per-window kernel
+        int st_max = 1, dmax_fit = 0;
+        std::vector<uint8_t> fit(dp.nd, 0);
         for (int j = 0; j < dp.nd; ++j) {
-            st_max = std::max(st_max, h.stride[j]);
-            const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
-            if ((int64_t)(16 + jrows + 2) * h.stride[j] + 32 > buf) fits = false;
+            const int st = h.stride[j], d = h.dpts[j];
+            const int jrows = (d + st - 1) / st;
+            fit[j] = buf > 0 && (int64_t)(16 + jrows + 2) * st + 32 <= buf &&
+                     (int64_t)d + 3 * st + 96 + 64 <= buf;
+            if (!fit[j]) continue;
+            st_max = std::max(st_max, st);
+            dmax_fit = std::max(dmax_fit, d);
         }
-        const int64_t len = ((int64_t)buf - h.dmax - 3 * (int64_t)st_max - 96) & ~int64_t(63);
-        pl->tile_ok = fits && len >= 64;
+        const int64_t len = ((int64_t)buf - dmax_fit - 3 * (int64_t)st_max - 96) & ~int64_t(63);
+        pl->tile_ok = dmax_fit > 0 && len >= 64;
         std::vector<int32_t> var(dp.nd, tiles::kWin16), ncs(dp.nd, 32);
         std::vector<int64_t> off2(dp.nd, 0);
         std::vector<float2> t2;
@@ -1434,6 +1442,11 @@ gtls_status create_device(gtls_plan* pl)
                 const int64_t m_total = (n + st - 1) / st;
                 const int nwin = (int)std::min<int64_t>(m_total, (len + st - 1) / st);
                 pick_config_host(st, nwin, var[j], ncs[j]);
+                if (!fit[j]) {
+                    var[j] = tiles::kWindowOnly;
+                    ncs[j] = 32;
+                    pl->has_window_only = true;
+                }
                 off2[j] = pos2;
                 if (tiles::variant_colpair(var[j]) || var[j] == tiles::kScalar15)
                     pos2 += h.dpts[j] + (tiles::kMaxRing + 2) * (int64_t)st + 64;
@@ -1462,6 +1475,7 @@ gtls_status create_device(gtls_plan* pl)
             }
         }
         GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_variant), var));
+        pl->variant_host = var;
         GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_nc), ncs));
         GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tmpl2_off), off2));
         if (t2.empty()) t2.assign(1, make_float2(0.0f, 0.0f));
@@ -1542,21 +1556,30 @@ gtls_status create_device(gtls_plan* pl)
                 for (int k = 0; k < h.dpts[j]; ++k) t21[(size_t)(off1[j] + k)] = make_float2(tj[k], 1.0f);
             }
             GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.stride), ones));
-            GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_variant), var1));
             GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_nc), ones));
             GTLS_TRY(upload(pl, const_cast<int64_t**>(&pl->dp_ref.tmpl2_off), off1));
             GTLS_TRY(upload(pl, const_cast<float2**>(&pl->dp_ref.tmpl2), t21));
             GTLS_TRY(dev_alloc(pl, &pl->dq.plist, pl->refine_k));
             if (pl->tile_ok) {
-                bool fits1 = true;
-                for (int j = 0; j < dp.nd; ++j)
-                    if ((int64_t)(16 + h.dpts[j] + 2) + 32 > pl->tile_buf) fits1 = false;
-                const int64_t len1 = ((int64_t)pl->tile_buf - h.dmax - 3 - 96) & ~int64_t(63);
-                if (!fits1 || len1 < 64)
+                // T0 step 1: durations whose rows or 64-window tile do not fit are
+                // searched by the one-thread-per-window kernel
+                int dmax1 = 0;
+                for (int j = 0; j < dp.nd; ++j) {
+                    const int d = h.dpts[j];
+                    if ((int64_t)(16 + d + 2) + 32 <= pl->tile_buf && (int64_t)d + 3 + 96 + 64 <= pl->tile_buf)
+                        dmax1 = std::max(dmax1, d);
+                    else {
+                        var1[j] = tiles::kWindowOnly;
+                        pl->has_window_only_ref = true;
+                    }
+                }
+                const int64_t len1 = ((int64_t)pl->tile_buf - dmax1 - 3 - 96) & ~int64_t(63);
+                if (dmax1 == 0 || len1 < 64)
                     return fail(GTLS_ERR_INVALID_ARG, "durations too long for the refinement tiles");
                 pl->tile_len_ref = (int)len1;
                 pl->tile_count_ref = (int)((n + len1 - 1) / len1);
             }
+            GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_variant), var1));
         }
         GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
     }
@@ -1657,8 +1680,8 @@ gtls_status stage_mark(Ctx& c, int stage)
 
 // One wave: fold + sort, every window, per-period results.  `counter` must
 // be zero when the window kernel starts (reset here when reset_counter).
-gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weighted, unsigned int* counter,
-                      bool reset_counter, int64_t max_n, int max_kept)
+gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weighted, bool window_only,
+                      unsigned int* counter, bool reset_counter, int64_t max_n, int max_kept)
 {
     const DevSet& ds = ref ? c.set_ref : c.set;
     k_fold_sort<<<sm.slots, kFoldThreads, c.fold_smem, c.st>>>(ds, sm, c.dk);
@@ -1670,10 +1693,16 @@ gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weig
         const int bytes = buf * (int)(weighted ? sizeof(float2) : sizeof(float));
         k_window_tiles<<<c.n_sm * tiles::kCtasPerSm, tiles::kThreads, bytes, c.st>>>(ds, sm, c.dk, buf,
                                                                                    weighted ? 1 : 0, counter);
-    } else {
+    }
+    if (!tiled || window_only) {
+        // every duration, or (next to the tiled kernel) those marked kWindowOnly
         dim3 grid((unsigned)((max_n + kSearchThreads - 1) / kSearchThreads), (unsigned)max_kept,
                   (unsigned)sm.slots);
-        k_window_search<<<grid, kSearchThreads, 0, c.st>>>(ds, sm, c.dk);
+        k_window_search<<<grid, kSearchThreads, 0, c.st>>>(ds, sm, c.dk, tiled ? 1 : 0);
+        if (tiled) {
+            GTLS_CUDA(cudaGetLastError());
+            c.launches += 1;
+        }
     }
     GTLS_CUDA(cudaGetLastError());
     GTLS_TRY(stage_mark(c, kStageWindow));
@@ -1798,7 +1827,8 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     for (int p0 = 0; p0 < dp.np; p0 += dk.chunk) {
         const int cnt = std::min<int>(dk.chunk, dp.np - p0);
         GTLS_TRY(wave_pass(c, false, single_wave(p0, cnt, wtiled ? pl->tile_count_w : pl->tile_count, false),
-                           tiled || wtiled, wtiled, pl->tile_counter, true, n, h.max_kept));
+                           tiled || wtiled, wtiled, tiled && pl->has_window_only, pl->tile_counter, true, n,
+                           h.max_kept));
     }
     GTLS_TRY(sr_sde_pass(c));
     // two-stage T0 search (Sect. 2.5): the refine_k best periods by SDE(P)
@@ -1813,7 +1843,7 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
         for (int r0 = 0; r0 < kref; r0 += dk.chunk) {
             const int cnt = std::min<int>(dk.chunk, kref - r0);
             GTLS_TRY(wave_pass(c, true, single_wave(r0, cnt, pl->tile_count_ref, true), tiled, false,
-                               pl->tile_counter, true, n, h.max_kept));
+                               tiled && pl->has_window_only_ref, pl->tile_counter, true, n, h.max_kept));
         }
         GTLS_TRY(sr_sde_pass(c));
     }
@@ -1842,6 +1872,7 @@ struct BatchWave {
     SlotMap sm;
     bool tiled;
     bool weighted;
+    bool window_only;   // some curve of the wave has durations marked kWindowOnly
     bool ref;
     int64_t max_n;
     int max_kept;
@@ -1943,16 +1974,24 @@ void batch_tiles(gtls_batch* b, int buf)
             b->tiles_host[i].count_w = pl->tile_count_w;
         }
         if (!pl->tile_ok) continue;
-        int st_max = 1;
+        // the plan's tiled durations (not kWindowOnly) must fit this buffer
+        int st_max = 1, dmax_t = 0, dmax1 = 0;
         bool fits = true, fits1 = true;
         for (size_t j = 0; j < h.dpts.size(); ++j) {
-            st_max = std::max(st_max, h.stride[j]);
-            const int jrows = (h.dpts[j] + h.stride[j] - 1) / h.stride[j];
-            if ((int64_t)(16 + jrows + 2) * h.stride[j] + 32 > buf) fits = false;
-            if ((int64_t)(16 + h.dpts[j] + 2) + 32 > buf) fits1 = false;
+            const int st = h.stride[j], d = h.dpts[j];
+            if (pl->variant_host[j] != tiles::kWindowOnly) {
+                st_max = std::max(st_max, st);
+                dmax_t = std::max(dmax_t, d);
+                const int jrows = (d + st - 1) / st;
+                if ((int64_t)(16 + jrows + 2) * st + 32 > buf || (int64_t)d + 3 * st + 96 + 64 > buf) fits = false;
+            }
+            if ((int64_t)(16 + d + 2) + 32 <= buf && (int64_t)d + 3 + 96 + 64 <= buf) dmax1 = std::max(dmax1, d);
+            else fits1 = false;   // every duration must fit the refinement tiles at this buffer
         }
-        const int64_t len = ((int64_t)buf - h.dmax - 3 * (int64_t)st_max - 96) & ~int64_t(63);
-        const int64_t len1 = ((int64_t)buf - h.dmax - 3 - 96) & ~int64_t(63);
+        if (pl->has_window_only_ref) fits1 = false;   // refinement tiles sized at the plan's own buffer only
+        const int64_t len = ((int64_t)buf - dmax_t - 3 * (int64_t)st_max - 96) & ~int64_t(63);
+        const int64_t len1 = ((int64_t)buf - dmax1 - 3 - 96) & ~int64_t(63);
+        if (dmax1 == 0) fits1 = false;
         if (fits && len >= 64) {
             b->fits[i] = 1;
             b->tiles_host[i].len = (int32_t)len;
@@ -1980,6 +2019,7 @@ void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, 
         w = BatchWave{};
         w.tiled = tiled;
         w.weighted = weighted;
+        w.window_only = false;
         w.ref = ref;
         w.sm.from_list = ref ? 1 : 0;
     };
@@ -1998,6 +2038,8 @@ void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, 
             w.sm.items += take * tiles_pp;
             w.max_n = std::max<int64_t>(w.max_n, h.n);
             w.max_kept = std::max(w.max_kept, h.max_kept);
+            const gtls_plan* pl = b->plans[r.lc];
+            if (tiled && !weighted && (ref ? pl->has_window_only_ref : pl->has_window_only)) w.window_only = true;
             done += take;
         }
     }
@@ -2075,16 +2117,16 @@ gtls_status batch_enqueue(gtls_batch* b, Ctx& c, const std::vector<BatchWave>& c
     GTLS_CUDA(cudaMemsetAsync(b->counters, 0, std::max(1, tiled_waves) * sizeof(unsigned int), c.st));
     int ci = 0;
     for (const BatchWave& w : coarse)
-        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, w.weighted, b->counters + (w.tiled ? ci++ : 0), false,
-                           w.max_n, w.max_kept));
+        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, w.weighted, w.window_only, b->counters + (w.tiled ? ci++ : 0),
+                           false, w.max_n, w.max_kept));
     GTLS_TRY(sr_sde_pass(c));
     k_topk<<<c.n_lc, 1024, c.topk_smem, c.st>>>(c.set, 0);
     GTLS_CUDA(cudaGetLastError());
     c.launches += 1;
     if (!refine.empty()) {
         for (const BatchWave& w : refine)
-            GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, w.weighted, b->counters + (w.tiled ? ci++ : 0), false,
-                               w.max_n, w.max_kept));
+            GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, w.weighted, w.window_only,
+                               b->counters + (w.tiled ? ci++ : 0), false, w.max_n, w.max_kept));
         GTLS_TRY(sr_sde_pass(c));
     }
     k_best<<<c.n_lc, 1024, 0, c.st>>>(c.set, 0, b->results, b->checks);
@@ -2359,7 +2401,7 @@ gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, cons
                 if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = fail(GTLS_ERR_CUDA, "cudaEventRecord");
                 int ci = 0;
                 for (const BatchWave& w : waves) {
-                    s = wave_pass(c, false, w.sm, true, false, b->counters + ci++, true, w.max_n, w.max_kept);
+                    s = wave_pass(c, false, w.sm, true, false, false, b->counters + ci++, true, w.max_n, w.max_kept);
                     if (s != GTLS_OK) break;
                 }
             }

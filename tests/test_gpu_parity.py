@@ -331,3 +331,24 @@ def test_flat_light_curve():
     assert np.all(out["depth"] == 0.0) and np.all(out["sr"] == 1.0) and np.all(out["sde"] == 0.0)
     assert res.snr == 0.0
     pl.close()
+
+
+def test_durations_longer_than_a_tile_take_the_window_kernel():
+    # 260,000 points: at short periods the capped durations (~39,000 points)
+    # exceed any shared-memory tile; those durations go to the
+    # one-thread-per-window kernel, the others stay on the tiled kernel
+    n = 260000
+    rng = np.random.default_rng(14)
+    t = np.sort(rng.uniform(0.0, 1800.0, n))
+    y = 1.0 + rng.normal(0, 2e-4, n)
+    dy = np.full(n, 2e-4)
+    periods = np.array([0.55, 0.9, 2.0, 45.0])
+    base = float(t[-1] - t[0])
+    op = gh.oracle_plan_for(n, base, periods_days=periods)
+    assert op.dur_pts.max() > 30000
+    r_or = osr.search_periods(op, t, y, dy)
+    pl = gh.plan_for(n, base, periods_days=periods)
+    res, out = gh.gpu_search(pl, t, y, dy)
+    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_argmins(op, t, y, dy, r_or, out)
+    pl.close()
