@@ -793,12 +793,12 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
             c.j = t.j;
             c.pf = dk.pf + (int64_t)slot * dk.pad_stride;
             switch (t.variant) {
-            case kWin16: warp_task_winpair<16, 4>(c, lane, best); break;
-            case kCol16: warp_task_colpair<16, 4>(c, lane, best); break;
-            case kCol15: warp_task_colpair<15, 5>(c, lane, best); break;
-            case kCol12: warp_task_colpair<12, 4>(c, lane, best); break;
-            case kWeighted15: warp_task_weighted<15, 5>(c, lane, best); break;
-            default: warp_task_scalar<15, 5>(c, lane, best); break;
+            case kWin16: warp_task_winpair<16, 3>(c, lane, best); break;
+            case kCol16: warp_task_colpair<16, 3>(c, lane, best); break;
+            case kCol15: warp_task_colpair<15, 4>(c, lane, best); break;
+            case kCol12: warp_task_colpair<12, 3>(c, lane, best); break;
+            case kWeighted15: warp_task_weighted<15, 4>(c, lane, best); break;
+            default: warp_task_scalar<15, 4>(c, lane, best); break;
             }
         }
 #pragma unroll

@@ -28,11 +28,16 @@
 //                 (T0 steps that are multiples of 32);
 //     scalar<15>  T0 steps 1, 2, 4, 8, 16 (one column per lane): each FFMA2
 //                 accumulates (C1, S) of one window from a (s_k, 1) table.
-//   Each variant is one unrolled loop of W rows (a uniform exit test per
-//   row), which keeps the kernel's code small enough for the instruction
-//   caches.
+//   Each variant walks the J rows in blocks of W (the unroll period of the
+//   data ring): full blocks run without exit tests, the last partial block
+//   tests once per row (a uniform test).
 //   Templates are followed by zeros, so every lane runs the same J steps
-//   and template rows can be fetched several rows ahead (register ring).
+//   and template rows can be fetched R rows ahead into a register ring of
+//   R + 1 slots: the load of row u + R goes to the slot that row u - 1 has
+//   freed, never to the one row u is multiplied with, so the registers keep
+//   their roles from row to row (a ring of R slots makes the compiler rename
+//   and copy a slot every row).  R + 1 divides W, so each block of W rows
+//   starts with the same slot assignment.
 //   The nc lanes of a block combine their partial sums by recursive halving
 //   (each exchange halves the values a lane holds), so every lane ends with
 //   exactly its W / nc windows, finishes them and keeps a packed running
@@ -238,12 +243,32 @@ __device__ __forceinline__ int block_start(const WinCtx& c, int b, int w, bool& 
     return max(c.m_a, min(m0, c.hi_start));
 }
 
+// Rows jj .. jj + cnt - 1 of one column (cnt = W unless !kFull): row u is
+// multiplied into the W window sums (acc[w] += p[(w + u) % W] x template row),
+// then its data slot takes row u + W and its template slot row u + R.
+template <int W, int R, bool kFull>
+__device__ __forceinline__ void colpair_rows(float2 (&acc)[W], float2 (&p)[W], float2 (&ring)[R + 1],
+                                             const float2*& tp, const float*& an, int st, int nc, int cnt)
+{
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        if (!kFull && u >= cnt) break;
+        ring[(u + R) % (R + 1)] = __ldg(tp);     // row u + R (zero padded past D)
+        tp += st;
+        const float2 tcur = ring[u % (R + 1)];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+        p[u].x = an[0];
+        p[u].y = an[nc];
+        an += st;
+    }
+}
+
 // Column pairs: acc[w] = (column rho, column rho + nc) partial sums of window w.
-// Template rows are fetched R rows ahead into a register ring (R divides W).
 template <int W, int R>
 __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long& best)
 {
-    static_assert(W % R == 0, "ring length must divide the unroll period");
+    static_assert(W % (R + 1) == 0, "template ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -259,7 +284,7 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
         for (int r = 0; r < R; ++r) nxt[r] = __ldg(c.tg2 + cl + r * st);
         for (int rho = cl; rho < st; rho += 2 * nc) {
             const float* a = abase + rho;
-            float2 ring[R];
+            float2 ring[R + 1];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 ring[r] = nxt[r];
@@ -273,20 +298,9 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
                 p[w].y = a[w * st + nc];
             }
             const float* an = a + W * st;
-            for (int jj = 0; jj < jrows; jj += W) {
-#pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    if (jj + u >= jrows) break;
-                    const float2 tcur = ring[u % R];
-                    ring[u % R] = __ldg(tp);     // row jj + u + R (zero padded past D)
-                    tp += st;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
-                    p[u].x = an[0];
-                    p[u].y = an[nc];
-                    an += st;
-                }
-            }
+            int jj = 0;
+            for (; jj + W <= jrows; jj += W) colpair_rows<W, R, true>(acc, p, ring, tp, an, st, nc, W);
+            if (jj < jrows) colpair_rows<W, R, false>(acc, p, ring, tp, an, st, nc, jrows - jj);
         }
     }
     float tot[W];
@@ -295,13 +309,33 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
     reduce_finish<W>(c, tot, mb, active, lane, best);
 }
 
+// Rows of one column for window pairs (H = W / 2 rows per block): acc[w]
+// holds windows w and w + H, p[w] the rows w and w + H ahead.
+template <int H, int R, bool kFull>
+__device__ __forceinline__ void winpair_rows(float2 (&acc)[H], float2 (&p)[H], float (&ring)[R + 1],
+                                             const float*& tp, const float*& an, int st, int cnt)
+{
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        if (!kFull && u >= cnt) break;
+        ring[(u + R) % (R + 1)] = __ldg(tp);
+        tp += st;
+        const float tv = ring[u % (R + 1)];
+        const float2 t2 = make_float2(tv, tv);
+#pragma unroll
+        for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
+        p[u].x = p[u].y;
+        p[u].y = *an;
+        an += st;
+    }
+}
+
 // Window pairs: acc[w] = (window w, window w + W/2) partial sums of one column.
-// Template rows come R rows ahead from a register ring (R divides W/2).
 template <int W, int R>
 __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long& best)
 {
     constexpr int H = W / 2;
-    static_assert(H % R == 0, "ring length must divide the unroll period");
+    static_assert(H % (R + 1) == 0, "template ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -317,7 +351,7 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
         for (int r = 0; r < R; ++r) nxt[r] = __ldg(c.tg + cl + r * st);
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
-            float ring[R];
+            float ring[R + 1];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 ring[r] = nxt[r];
@@ -331,21 +365,9 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
                 p[w].y = a[(w + H) * st];
             }
             const float* an = a + W * st;
-            for (int jj = 0; jj < jrows; jj += H) {
-#pragma unroll
-                for (int u = 0; u < H; ++u) {
-                    if (jj + u >= jrows) break;
-                    const float tv = ring[u % R];
-                    ring[u % R] = __ldg(tp);
-                    tp += st;
-                    const float2 t2 = make_float2(tv, tv);
-#pragma unroll
-                    for (int w = 0; w < H; ++w) acc[w] = __ffma2_rn(p[(w + u) % H], t2, acc[w]);
-                    p[u].x = p[u].y;
-                    p[u].y = *an;
-                    an += st;
-                }
-            }
+            int jj = 0;
+            for (; jj + H <= jrows; jj += H) winpair_rows<H, R, true>(acc, p, ring, tp, an, st, H);
+            if (jj < jrows) winpair_rows<H, R, false>(acc, p, ring, tp, an, st, jrows - jj);
         }
     }
     float tot[W];
@@ -357,6 +379,26 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
     reduce_finish<W>(c, tot, mb, active, lane, best);
 }
 
+// Rows of one column for the (C1, S) pairs: the data value is duplicated
+// into both halves of its slot.
+template <int W, int R, bool kFull>
+__device__ __forceinline__ void scalar_rows(float2 (&acc)[W], float2 (&p)[W], float2 (&ring)[R + 1],
+                                            const float2*& tp, const float*& an, int st, int cnt)
+{
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        if (!kFull && u >= cnt) break;
+        ring[(u + R) % (R + 1)] = __ldg(tp);
+        tp += st;
+        const float2 tcur = ring[u % (R + 1)];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+        const float v = *an;
+        p[u] = make_float2(v, v);
+        an += st;
+    }
+}
+
 // Small T0 steps (st = nc = 1, 2, 4, 8, 16): one column per lane.  Each
 // FFMA2 accumulates (C1, S) = (sum r s_k, sum r) of one window and column
 // from the pair table (s_k, 1); the nc columns are then combined, so the
@@ -364,7 +406,7 @@ __device__ void warp_task_winpair(const WinCtx& c, int lane, unsigned long long&
 template <int W, int R>
 __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& best)
 {
-    static_assert(W % R == 0, "ring length must divide the unroll period");
+    static_assert(W % (R + 1) == 0, "template ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -378,7 +420,7 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
         for (int rho = cl; rho < st; rho += c.nc) {
             const float* a = abase + rho;
             const float2* tp = c.tg2 + rho;
-            float2 ring[R];
+            float2 ring[R + 1];
 #pragma unroll
             for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
             tp += R * st;
@@ -389,20 +431,9 @@ __device__ void warp_task_scalar(const WinCtx& c, int lane, unsigned long long& 
                 p[w] = make_float2(v, v);
             }
             const float* an = a + W * st;
-            for (int jj = 0; jj < jrows; jj += W) {
-#pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    if (jj + u >= jrows) break;
-                    const float2 tcur = ring[u % R];
-                    ring[u % R] = __ldg(tp);
-                    tp += st;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
-                    const float v = *an;
-                    p[u] = make_float2(v, v);
-                    an += st;
-                }
-            }
+            int jj = 0;
+            for (; jj + W <= jrows; jj += W) scalar_rows<W, R, true>(acc, p, ring, tp, an, st, W);
+            if (jj < jrows) scalar_rows<W, R, false>(acc, p, ring, tp, an, st, jrows - jj);
         }
     }
     reduce_pair_finish<W>(c, acc, mb, active, lane, best);
@@ -452,6 +483,24 @@ __device__ __forceinline__ void reduce_weighted_finish(const WinCtx& c, const fl
     }
 }
 
+// Rows of one column of (w r, w) pairs.
+template <int W, int R, bool kFull>
+__device__ __forceinline__ void weighted_rows(float2 (&acc)[W], float2 (&p)[W], float2 (&ring)[R + 1],
+                                              const float2*& tp, const float2*& an, int st, int cnt)
+{
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        if (!kFull && u >= cnt) break;
+        ring[(u + R) % (R + 1)] = __ldg(tp);
+        tp += st;
+        const float2 tcur = ring[u % (R + 1)];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
+        p[u] = *an;
+        an += st;
+    }
+}
+
 // Per-point weights: nc lanes per window block (2^v for st = 2^v odd, or 16 /
 // 32: one block per half-warp / warp), each lane one column at a time; each
 // FFMA2 multiplies the staged pair (w r, w) of a point by the template pair
@@ -460,7 +509,7 @@ __device__ __forceinline__ void reduce_weighted_finish(const WinCtx& c, const fl
 template <int W, int R>
 __device__ void warp_task_weighted(const WinCtx& c, int lane, unsigned long long& best)
 {
-    static_assert(W % R == 0, "ring length must divide the unroll period");
+    static_assert(W % (R + 1) == 0, "template ring length must divide the unroll period");
     const int b = lane >> c.lg_nc;
     const int cl = lane & (c.nc - 1);
     bool active;
@@ -474,7 +523,7 @@ __device__ void warp_task_weighted(const WinCtx& c, int lane, unsigned long long
         for (int rho = cl; rho < st; rho += c.nc) {
             const float2* a = abase + rho;
             const float2* tp = c.tg2 + rho;
-            float2 ring[R];
+            float2 ring[R + 1];
 #pragma unroll
             for (int r = 0; r < R; ++r) ring[r] = __ldg(tp + r * st);
             tp += R * st;
@@ -482,19 +531,9 @@ __device__ void warp_task_weighted(const WinCtx& c, int lane, unsigned long long
 #pragma unroll
             for (int w = 0; w < W; ++w) p[w] = a[w * st];
             const float2* an = a + W * st;
-            for (int jj = 0; jj < jrows; jj += W) {
-#pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    if (jj + u >= jrows) break;
-                    const float2 tcur = ring[u % R];
-                    ring[u % R] = __ldg(tp);
-                    tp += st;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = __ffma2_rn(p[(w + u) % W], tcur, acc[w]);
-                    p[u] = *an;
-                    an += st;
-                }
-            }
+            int jj = 0;
+            for (; jj + W <= jrows; jj += W) weighted_rows<W, R, true>(acc, p, ring, tp, an, st, W);
+            if (jj < jrows) weighted_rows<W, R, false>(acc, p, ring, tp, an, st, jrows - jj);
         }
     }
     reduce_weighted_finish<W>(c, acc, mb, active, lane, best);
