@@ -20,6 +20,7 @@ struct DevPlan {
     int32_t time_exponent;
     int32_t idx_bits;
     int32_t bucket_log2;
+    int32_t fold_sb_log2;  // super-buckets of the staged fold (log2)
     int32_t max_kept;
     const double* periods;
     const int64_t* p_lat;
@@ -69,7 +70,6 @@ struct DevChunk {
     int64_t fold_stride;      // >= n
     int64_t pad_stride;       // >= n + dmax + margin (folded, padded arrays)
     unsigned long long* keys; // bucket-ordered fold keys
-    uint32_t* slot;           // arrival slot in the bucket
     int32_t* sidx;            // folded order -> original index
     float* rs;                // folded r, padded by the period's first D_m points
     float* ws;                // folded w (per-point weights only)

@@ -307,18 +307,261 @@ __global__ void k_curve_reduce(const double* __restrict__ dy, const int64_t* __r
 // ---------------------------------------------------------------------------
 // fold + sort + gather + prefix sums (one block per period)
 // ---------------------------------------------------------------------------
+//
+// The folded order is the order of the keys (rho << idx_bits | i).  Two
+// monotone functions of rho split it into buckets: fold_bucket (2^bucket_log2
+// buckets) and fold_fine (2^(sb_log2 + kFoldFineLog2) fine buckets, grouped
+// into 2^sb_log2 super-buckets of 2^kFoldFineLog2 each).
+//
+// Staged path (the common case): the keys are scattered once into global
+// memory in super-bucket order -- a few dozen write streams that fill whole
+// cache lines -- and every super-bucket (at most kFoldSegKeys keys) is then
+// bucket sorted, ranked, gathered and scanned in shared memory.  Global path
+// (a phase pile-up: some super-bucket too full for shared memory): the keys
+// are scattered into global memory in bucket order and runs of whole buckets
+// are ranked and scanned (in shared memory while a run fits, else in global
+// memory).
 
-__global__ void __launch_bounds__(kFoldThreads, kFoldMinBlocks)
-k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
+constexpr int kFoldFineLog2 = 11;   // fine buckets per super-bucket (log2)
+constexpr int kFoldMaxSbLog2 = 10;  // at most one super-bucket per fold thread
+
+__device__ __forceinline__ uint32_t fold_fine(long long rho, int sh, uint32_t mul, int fshift)
 {
-    extern __shared__ unsigned char smem[];
-    const int slot_id = blockIdx.x;
-    int lc, p;
-    if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
-    unsigned long long* const keys = dk.keys + (int64_t)slot_id * dk.fold_stride;
-    uint32_t* const slotv = dk.slot + (int64_t)slot_id * dk.fold_stride;
-    const DevPlan& dp = ds.plans[lc];
-    const DevCurve dc = ds.curves[lc];
+    return (uint32_t)((((unsigned long long)rho >> sh) * (unsigned long long)mul) >> fshift);
+}
+
+// Warp-aggregated increment of cnt[s] by one per lane of `active` (the lanes
+// calling it): returns the lane's slot, i.e. the counter's value before the
+// warp's increment plus the rank of the lane among lanes with the same s.
+__device__ __forceinline__ uint32_t agg_slot(uint32_t* cnt, uint32_t s, unsigned int active)
+{
+    const unsigned int peers = __match_any_sync(active, s);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&cnt[s], (uint32_t)__popc(peers));
+    base = __shfl_sync(active, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+struct FoldOut {
+    int32_t* sidx;
+    float* rs;
+    float* ws;
+    float* wrs;
+    long long* pf;
+    bool uniform;
+};
+
+// Rank keys[q] (q < len, staged in shared memory in bucket order) inside
+// their buckets, gather the folded curve into positions k0 + rank of the
+// outputs and the folded rfx into srfx[rank].  bucket_of(key, b) gives the
+// bucket b (false: skip the key); its keys occupy [e - cnt_of[b], e) of keys
+// with e = end_of[b] - end_base.
+template <typename BucketOf>
+__device__ __forceinline__ void fold_rank_gather(const unsigned long long* keys, uint32_t len, uint32_t k0,
+                                                 const uint32_t* cnt_of, const uint32_t* end_of,
+                                                 uint32_t end_base, BucketOf bucket_of, int ib,
+                                                 unsigned long long idx_mask,
+                                                 int64_t n, const DevCurve& dc, const FoldOut& o,
+                                                 long long* srfx)
+{
+    for (uint32_t q0 = threadIdx.x; q0 < len; q0 += kRankBatch * blockDim.x) {
+        uint32_t pos[kRankBatch];
+        int32_t idx[kRankBatch];
+#pragma unroll
+        for (int j = 0; j < kRankBatch; ++j) {
+            pos[j] = 0xffffffffu;
+            idx[j] = 0;
+            const uint32_t q = q0 + j * blockDim.x;
+            if (q >= len) continue;
+            const unsigned long long key = keys[q];
+            int b;
+            if (!bucket_of(key, b)) continue;
+            const uint32_t cnt = cnt_of[b], lo = end_of[b] - end_base - cnt;
+            if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)len + 1)) continue;
+            uint32_t rank = 0;
+            for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
+            const int32_t id = (int32_t)(key & idx_mask);
+            if (!in_range(dc.check, 7, lo + rank, len) || !in_range(dc.check, 8, id, n)) continue;
+            pos[j] = lo + rank;
+            idx[j] = id;
+        }
+        float rv[kRankBatch];
+        long long fv[kRankBatch];
+#pragma unroll
+        for (int j = 0; j < kRankBatch; ++j) {
+            rv[j] = pos[j] != 0xffffffffu ? dc.r32[idx[j]] : 0.0f;
+            fv[j] = pos[j] != 0xffffffffu ? dc.rfx[idx[j]] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kRankBatch; ++j) {
+            if (pos[j] == 0xffffffffu) continue;
+            const int64_t g = (int64_t)k0 + pos[j];
+            o.sidx[g] = idx[j];
+            o.rs[g] = rv[j];
+            srfx[pos[j]] = fv[j];
+            if (!o.uniform) {
+                o.ws[g] = dc.w32[idx[j]];
+                o.wrs[g] = dc.w32[idx[j]] * rv[j];
+            }
+        }
+    }
+}
+
+// pf[k0 + 1 + i] = carry + srfx[0] + ... + srfx[i] for i < len; carry
+// advances by the run's total.
+__device__ __forceinline__ void fold_scan_run(const long long* srfx, uint32_t len, uint32_t k0, long long* pf,
+                                              long long& carry, long long* warp_sums, long long* total)
+{
+    const int64_t span = (int64_t)blockDim.x * kScanPer;
+    for (int64_t base = 0; base < len; base += span) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
+        long long v[kScanPer];
+        long long run = 0;
+#pragma unroll
+        for (int u = 0; u < kScanPer; ++u) {
+            run += i0 + u < len ? srfx[i0 + u] : 0;
+            v[u] = run;
+        }
+        const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
+#pragma unroll
+        for (int u = 0; u < kScanPer; ++u)
+            if (i0 + u < len) pf[k0 + i0 + u + 1] = ex + v[u];
+        carry += *total;
+    }
+}
+
+// Staged path; false (nothing written) when a super-bucket holds more than
+// kFoldSegKeys points.
+__device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCurve& dc, int p,
+                            unsigned long long* keys, const FoldOut& o)
+{
+    const int64_t n = dp.n;
+    const long long P = dp.p_lat[p];
+    const float inv_p = dp.inv_p[p];
+    const int sh = dp.bucket_shift[p];
+    const uint32_t mul = dp.bucket_mul[p];
+    const int ib = dp.idx_bits;
+    const unsigned long long idx_mask = (1ull << ib) - 1ull;
+    const int sb_log2 = dp.fold_sb_log2;
+    const int nsb = 1 << sb_log2;
+    const int fshift = dp.bucket_log2 + 32 - (sb_log2 + kFoldFineLog2);
+    constexpr uint32_t kFineMask = (1u << kFoldFineLog2) - 1u;
+    static_assert((1 << kFoldFineLog2) % kFoldThreads == 0, "fine buckets split evenly over the threads");
+    static_assert((1 << kFoldMaxSbLog2) <= kFoldThreads, "one super-bucket count per thread");
+
+    long long* warp_sums = reinterpret_cast<long long*>(smem);
+    long long* total = warp_sums + 32;
+    unsigned long long* stage = reinterpret_cast<unsigned long long*>(total + 1);   // keys as read; later rfx
+    unsigned long long* sorted = stage + kFoldSegKeys;                            // keys in fine-bucket order
+    uint32_t* fcnt = reinterpret_cast<uint32_t*>(sorted + kFoldSegKeys);
+    uint32_t* fcur = fcnt + (1 << kFoldFineLog2);
+    uint32_t* sb_cnt = fcur + (1 << kFoldFineLog2);
+    uint32_t* sb_start = sb_cnt + (1 << kFoldMaxSbLog2);
+    uint32_t* sb_cur = sb_start + (1 << kFoldMaxSbLog2);
+    int* overflow = reinterpret_cast<int*>(sb_cur + (1 << kFoldMaxSbLog2));
+
+    for (int q = threadIdx.x; q < nsb; q += blockDim.x) sb_cnt[q] = 0;
+    if (threadIdx.x == 0) *overflow = 0;
+    __syncthreads();
+
+    // A. super-bucket of every point: counts, then the scatter (the loop
+    // bounds are block-uniform so that whole warps take the aggregated
+    // increments)
+    const int64_t bs = blockDim.x;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t g0 = 0; g0 < n; g0 += kFoldUnroll * bs) {
+            long long dl[kFoldUnroll];
+            float df[kFoldUnroll];
+#pragma unroll
+            for (int u = 0; u < kFoldUnroll; ++u) {
+                const int64_t i = g0 + u * bs + threadIdx.x;
+                dl[u] = i < n ? dc.d_lat[i] : 0;
+                df[u] = i < n ? dc.d_f[i] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kFoldUnroll; ++u) {
+                const int64_t i = g0 + u * bs + threadIdx.x;
+                const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
+                const uint32_t sb = fold_fine(rho, sh, mul, fshift) >> kFoldFineLog2;
+                const bool ok = i < n && in_range(dc.check, 2, rho, P) && in_range(dc.check, 1, sb, nsb);
+                const unsigned int active = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    const uint32_t slot = agg_slot(pass == 0 ? sb_cnt : sb_cur, sb, active);
+                    if (pass == 1 && in_range(dc.check, 4, slot, n))
+                        keys[slot] = ((unsigned long long)rho << ib) | (unsigned long long)i;
+                }
+            }
+        }
+        __syncthreads();
+        if (pass == 0) {
+            // super-bucket starts; any super-bucket too large for shared
+            // memory sends the period to the global path
+            const uint32_t c = threadIdx.x < nsb ? sb_cnt[threadIdx.x] : 0u;
+            if (c > (uint32_t)kFoldSegKeys) *overflow = 1;
+            const long long st = block_exclusive_scan(c, warp_sums, total);
+            if (threadIdx.x < nsb) {
+                sb_start[threadIdx.x] = (uint32_t)st;
+                sb_cur[threadIdx.x] = (uint32_t)st;
+            }
+            __syncthreads();
+            if (*overflow) return false;
+        }
+    }
+
+    // B. each super-bucket in shared memory
+    long long carry = 0;
+    if (threadIdx.x == 0) o.pf[0] = 0;
+    for (int sb = 0; sb < nsb; ++sb) {
+        const uint32_t k0 = sb_start[sb], len = sb_cnt[sb];
+        if (len == 0) continue;
+        for (int f = threadIdx.x; f < (1 << kFoldFineLog2); f += blockDim.x) fcnt[f] = 0;
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
+            const unsigned long long key = keys[k0 + q];
+            stage[q] = key;
+            atomicAdd(&fcnt[fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask], 1u);
+        }
+        __syncthreads();
+        {
+            constexpr int kPer = (1 << kFoldFineLog2) / kFoldThreads;
+            const int f0 = threadIdx.x * kPer;
+            long long local = 0;
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) local += fcnt[f0 + u];
+            long long run = block_exclusive_scan(local, warp_sums, total);
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                fcur[f0 + u] = (uint32_t)run;
+                run += fcnt[f0 + u];
+            }
+        }
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
+            const unsigned long long key = stage[q];
+            const uint32_t f = fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask;
+            const uint32_t d = atomicAdd(&fcur[f], 1u);   // fcur[f] ends as the end of bucket f
+            if (in_range(dc.check, 5, d, len)) sorted[d] = key;
+        }
+        __syncthreads();
+        long long* srfx = reinterpret_cast<long long*>(stage);
+        auto bucket_of = [&](unsigned long long key, int& f) {
+            f = (int)(fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask);
+            return true;
+        };
+        fold_rank_gather(sorted, len, k0, fcnt, fcur, 0u, bucket_of, ib, idx_mask, n, dc, o, srfx);
+        __syncthreads();
+        fold_scan_run(srfx, len, k0, o.pf, carry, warp_sums, total);
+        __syncthreads();   // the next super-bucket overwrites the staged keys and rfx
+    }
+    return true;
+}
+
+// Global path (see above).
+__device__ void fold_global(unsigned char* smem, const DevPlan& dp, const DevCurve& dc, int p,
+                            unsigned long long* keys, const FoldOut& o)
+{
     const int nb = 1 << dp.bucket_log2;
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
     uint32_t* start = hist + nb;
@@ -332,19 +575,12 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     const uint32_t mul = dp.bucket_mul[p];
     const int ib = dp.idx_bits;
     const unsigned long long idx_mask = (1ull << ib) - 1ull;
-    int32_t* sidx = dk.sidx + (int64_t)slot_id * dk.fold_stride;
-    float* rs = dk.rs + (int64_t)slot_id * dk.pad_stride;
-    float* ws = dk.ws ? dk.ws + (int64_t)slot_id * dk.pad_stride : nullptr;
-    float* wrs = dk.wrs ? dk.wrs + (int64_t)slot_id * dk.pad_stride : nullptr;
-    long long* pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
-    const bool uniform = dc.scal[2] > 0.0;
 
-    if (threadIdx.x == 0) ds.outs[lc].best[p] = ~0ull;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
 
-    // 1. lattice phase -> bucket, arrival slot inside the bucket (the loads
-    // of kFoldUnroll points are issued before their arithmetic)
+    // 1. bucket histogram (the loads of kFoldUnroll points are issued before
+    // their arithmetic)
     const int64_t bs = blockDim.x;
     for (int64_t i0 = threadIdx.x; i0 < n; i0 += kFoldUnroll * bs) {
         long long dl[kFoldUnroll];
@@ -361,7 +597,7 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
             if (i >= n) break;
             const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
             const uint32_t b = fold_bucket(rho, sh, mul);
-            slotv[i] = in_range(dc.check, 1, b, nb) && in_range(dc.check, 2, rho, P) ? atomicAdd(&hist[b], 1u) : 0u;
+            if (in_range(dc.check, 1, b, nb) && in_range(dc.check, 2, rho, P)) atomicAdd(&hist[b], 1u);
         }
     }
     __syncthreads();
@@ -380,17 +616,17 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     }
     __syncthreads();
 
-    // 3. scatter keys (phase << idx_bits | index) into bucket order
+    // 3. scatter keys (phase << idx_bits | index) into bucket order; the
+    // arrival order inside a bucket does not matter (the keys are ranked
+    // below), and start[b] ends as the end of bucket b
     for (int64_t i0 = threadIdx.x; i0 < n; i0 += kFoldUnroll * bs) {
         long long dl[kFoldUnroll];
         float df[kFoldUnroll];
-        uint32_t sl[kFoldUnroll];
 #pragma unroll
         for (int u = 0; u < kFoldUnroll; ++u) {
             const int64_t i = i0 + u * bs;
             dl[u] = i < n ? dc.d_lat[i] : 0;
             df[u] = i < n ? dc.d_f[i] : 0.0f;
-            sl[u] = i < n ? slotv[i] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < kFoldUnroll; ++u) {
@@ -399,7 +635,7 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
             const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
             const uint32_t b = fold_bucket(rho, sh, mul);
             if (!in_range(dc.check, 3, b, nb)) continue;
-            const long long dst = (long long)start[b] + sl[u];
+            const long long dst = (long long)atomicAdd(&start[b], 1u);
             if (in_range(dc.check, 4, dst, n))
                 keys[dst] = ((unsigned long long)rho << ib) | (unsigned long long)i;
         }
@@ -411,106 +647,56 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     // (pf[k+1] = sum_{u<=k} rfx).  A run holds at most kFoldSegKeys keys; its
     // keys and folded rfx are staged in shared memory, ranked and scanned
     // there, and pf is written once, coalesced.  A single bucket larger than
-    // that (a phase pile-up) is ranked and scanned in global memory.
+    // that is ranked and scanned in global memory.
     unsigned long long* const skeys = reinterpret_cast<unsigned long long*>(total + 1);
     long long* const srfx = reinterpret_cast<long long*>(skeys + kFoldSegKeys);
     const int64_t span = bs * kScanPer;
     long long carry = 0;   // sum of rfx over the folded positions before the run
-    if (threadIdx.x == 0) pf[0] = 0;
+    if (threadIdx.x == 0) o.pf[0] = 0;
+    auto begin_of = [&](int b) -> uint32_t { return b < nb ? start[b] - hist[b] : (uint32_t)n; };
     for (int b_lo = 0; b_lo < nb;) {
-        const uint32_t k0 = start[b_lo];
-        auto end_of = [&](int b) -> uint32_t { return b < nb ? start[b] : (uint32_t)n; };
+        const uint32_t k0 = begin_of(b_lo);
         int b_hi = b_lo + 1;
-        if (end_of(b_hi) - k0 <= (uint32_t)kFoldSegKeys) {
+        if (begin_of(b_hi) - k0 <= (uint32_t)kFoldSegKeys) {
             int lo = b_hi, hi = nb;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (end_of(mid) - k0 <= (uint32_t)kFoldSegKeys) lo = mid;
+                if (begin_of(mid) - k0 <= (uint32_t)kFoldSegKeys) lo = mid;
                 else hi = mid - 1;
             }
             b_hi = lo;
         }
-        const uint32_t k1 = end_of(b_hi);
+        const uint32_t k1 = begin_of(b_hi);
         const uint32_t len = k1 - k0;
         if (len <= (uint32_t)kFoldSegKeys) {
             for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) skeys[q] = keys[k0 + q];
             __syncthreads();
-            for (uint32_t q0 = threadIdx.x; q0 < len; q0 += kRankBatch * blockDim.x) {
-                uint32_t pos[kRankBatch];
-                int32_t idx[kRankBatch];
-#pragma unroll
-                for (int j = 0; j < kRankBatch; ++j) {
-                    pos[j] = 0xffffffffu;
-                    idx[j] = 0;
-                    const uint32_t q = q0 + j * blockDim.x;
-                    if (q >= len) continue;
-                    const unsigned long long key = skeys[q];
-                    const uint32_t b = fold_bucket((long long)(key >> ib), sh, mul);
-                    if (!in_range(dc.check, 5, (long long)b - b_lo, b_hi - b_lo)) continue;
-                    const uint32_t lo = start[b] - k0, cnt = hist[b];
-                    if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)len + 1)) continue;
-                    uint32_t rank = 0;
-                    for (uint32_t u = 0; u < cnt; ++u) rank += skeys[lo + u] < key ? 1u : 0u;
-                    const int32_t id = (int32_t)(key & idx_mask);
-                    if (!in_range(dc.check, 7, lo + rank, len) || !in_range(dc.check, 8, id, n)) continue;
-                    pos[j] = lo + rank;
-                    idx[j] = id;
-                }
-                float rv[kRankBatch];
-                long long fv[kRankBatch];
-#pragma unroll
-                for (int j = 0; j < kRankBatch; ++j) {
-                    rv[j] = pos[j] != 0xffffffffu ? dc.r32[idx[j]] : 0.0f;
-                    fv[j] = pos[j] != 0xffffffffu ? dc.rfx[idx[j]] : 0;
-                }
-#pragma unroll
-                for (int j = 0; j < kRankBatch; ++j) {
-                    if (pos[j] == 0xffffffffu) continue;
-                    const int64_t g = (int64_t)k0 + pos[j];
-                    sidx[g] = idx[j];
-                    rs[g] = rv[j];
-                    srfx[pos[j]] = fv[j];
-                    if (!uniform) {
-                        ws[g] = dc.w32[idx[j]];
-                        wrs[g] = dc.w32[idx[j]] * rv[j];
-                    }
-                }
-            }
+            auto bucket_of = [&](unsigned long long key, int& b) {
+                b = (int)fold_bucket((long long)(key >> ib), sh, mul);
+                return in_range(dc.check, 5, (long long)b - b_lo, b_hi - b_lo);
+            };
+            fold_rank_gather(skeys, len, k0, hist, start, k0, bucket_of, ib, idx_mask, n, dc, o, srfx);
             __syncthreads();
-            for (int64_t base = 0; base < len; base += span) {
-                const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
-                long long v[kScanPer];
-                long long run = 0;
-#pragma unroll
-                for (int u = 0; u < kScanPer; ++u) {
-                    run += i0 + u < len ? srfx[i0 + u] : 0;
-                    v[u] = run;
-                }
-                const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
-#pragma unroll
-                for (int u = 0; u < kScanPer; ++u)
-                    if (i0 + u < len) pf[k0 + i0 + u + 1] = ex + v[u];
-                carry += *total;
-            }
+            fold_scan_run(srfx, len, k0, o.pf, carry, warp_sums, total);
             __syncthreads();   // the next run overwrites the staged keys and rfx
         } else {
             for (int64_t q = k0 + threadIdx.x; q < k1; q += blockDim.x) {
                 const unsigned long long key = keys[q];
                 const uint32_t b = fold_bucket((long long)(key >> ib), sh, mul);
                 if (!in_range(dc.check, 5, (long long)b - b_lo, b_hi - b_lo)) continue;
-                const uint32_t lo = start[b], cnt = hist[b];
+                const uint32_t cnt = hist[b], lo = start[b] - cnt;
                 if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)k1 + 1)) continue;
                 uint32_t rank = 0;
                 for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
                 const uint32_t g = lo + rank;
                 const int32_t id = (int32_t)(key & idx_mask);
                 if (!in_range(dc.check, 7, g, n) || !in_range(dc.check, 8, id, n)) continue;
-                sidx[g] = id;
-                rs[g] = dc.r32[id];
-                pf[g + 1] = dc.rfx[id];
-                if (!uniform) {
-                    ws[g] = dc.w32[id];
-                    wrs[g] = dc.w32[id] * dc.r32[id];
+                o.sidx[g] = id;
+                o.rs[g] = dc.r32[id];
+                o.pf[g + 1] = dc.rfx[id];
+                if (!o.uniform) {
+                    o.ws[g] = dc.w32[id];
+                    o.wrs[g] = dc.w32[id] * dc.r32[id];
                 }
             }
             __syncthreads();
@@ -520,31 +706,57 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
                 long long run = 0;
 #pragma unroll
                 for (int u = 0; u < kScanPer; ++u) {
-                    run += i0 + u < k1 ? pf[i0 + u + 1] : 0;
+                    run += i0 + u < k1 ? o.pf[i0 + u + 1] : 0;
                     v[u] = run;
                 }
                 const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
 #pragma unroll
                 for (int u = 0; u < kScanPer; ++u)
-                    if (i0 + u < k1) pf[i0 + u + 1] = ex + v[u];
+                    if (i0 + u < k1) o.pf[i0 + u + 1] = ex + v[u];
                 carry += *total;
             }
             __syncthreads();
         }
         b_lo = b_hi;
     }
+}
 
-    // 6. padding: the first D_m folded points repeat after position N-1
+__global__ void __launch_bounds__(kFoldThreads, kFoldMinBlocks)
+k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
+{
+    extern __shared__ unsigned char smem[];
+    const int slot_id = blockIdx.x;
+    int lc, p;
+    if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
+    unsigned long long* const keys = dk.keys + (int64_t)slot_id * dk.fold_stride;
+    const DevPlan& dp = ds.plans[lc];
+    const DevCurve dc = ds.curves[lc];
+    FoldOut o;
+    o.sidx = dk.sidx + (int64_t)slot_id * dk.fold_stride;
+    o.rs = dk.rs + (int64_t)slot_id * dk.pad_stride;
+    o.ws = dk.ws ? dk.ws + (int64_t)slot_id * dk.pad_stride : nullptr;
+    o.wrs = dk.wrs ? dk.wrs + (int64_t)slot_id * dk.pad_stride : nullptr;
+    o.pf = dk.pf + (int64_t)slot_id * dk.pad_stride;
+    o.uniform = dc.scal[2] > 0.0;
+    if (threadIdx.x == 0) ds.outs[lc].best[p] = ~0ull;
+
+    if (!fold_staged(smem, dp, dc, p, keys, o)) {
+        __syncthreads();   // the global path reuses the shared memory
+        fold_global(smem, dp, dc, p, keys, o);
+    }
+
+    // padding: the first D_m folded points repeat after position N-1
+    const int64_t n = dp.n;
     const int64_t dm = dp.dmax_p[p];
-    const long long tot = pf[n];
+    const long long tot = o.pf[n];
     for (int64_t k = threadIdx.x; k < dm + kPadMargin; k += blockDim.x) {
         const bool real = k < dm;
-        rs[n + k] = real ? rs[k] : 0.0f;
-        if (!uniform) {
-            ws[n + k] = real ? ws[k] : 0.0f;
-            wrs[n + k] = real ? wrs[k] : 0.0f;
+        o.rs[n + k] = real ? o.rs[k] : 0.0f;
+        if (!o.uniform) {
+            o.ws[n + k] = real ? o.ws[k] : 0.0f;
+            o.wrs[n + k] = real ? o.wrs[k] : 0.0f;
         }
-        if (real) pf[n + k + 1] = tot + pf[k + 1];
+        if (real) o.pf[n + k + 1] = tot + o.pf[k + 1];
     }
 }
 
@@ -1253,9 +1465,15 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
 
 int fold_smem_bytes(int bucket_log2)
 {
-    // histogram and starts, scan scratch, staged keys and folded rfx
-    return (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long) +
-           kFoldSegKeys * (int)(sizeof(unsigned long long) + sizeof(long long));
+    // global path: histogram and starts, scan scratch, staged keys and folded rfx
+    const int global_path = (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long) +
+                            kFoldSegKeys * (int)(sizeof(unsigned long long) + sizeof(long long));
+    // staged path: scan scratch, staged and sorted keys, fine-bucket counts
+    // and ends, super-bucket counts, starts and cursors, overflow flag
+    const int staged = 33 * (int)sizeof(long long) + 2 * kFoldSegKeys * (int)sizeof(unsigned long long) +
+                       (2 << kFoldFineLog2) * (int)sizeof(uint32_t) +
+                       3 * (1 << kFoldMaxSbLog2) * (int)sizeof(uint32_t) + (int)sizeof(int);
+    return std::max(global_path, staged);
 }
 
 int topk_smem_bytes(int, int)
@@ -1302,6 +1520,12 @@ gtls_status create_device(gtls_plan* pl)
     dp.time_exponent = h.time_exponent;
     dp.idx_bits = h.idx_bits;
     dp.bucket_log2 = h.bucket_log2;
+    {
+        // super-buckets of the staged fold: about 4096 points each on average
+        int sb = 0;
+        while (sb < kFoldMaxSbLog2 && (h.n >> sb) > kFoldSegKeys / 2) ++sb;
+        dp.fold_sb_log2 = sb;
+    }
     dp.max_kept = h.max_kept;
     dp.median_half = h.median_window / 2;
     if (median_outs(dp.median_half) < 32)
@@ -1364,7 +1588,7 @@ gtls_status create_device(gtls_plan* pl)
     DevChunk& dk = pl->dk;
     dk.fold_stride = (n + 31) & ~int64_t(31);
     dk.pad_stride = (n + h.dmax + kPadMargin + 31) & ~int64_t(31);
-    const int64_t per_period = dk.fold_stride * (8 + 4 + 4) + dk.pad_stride * (4 + 4 + 4 + 8);
+    const int64_t per_period = dk.fold_stride * (8 + 4) + dk.pad_stride * (4 + 4 + 4 + 8);
     const int64_t budget = int64_t(1) << 31;  // 2 GiB of chunk scratch
     int64_t chunk = std::max<int64_t>(1, budget / per_period);
     chunk = std::min<int64_t>(chunk, 1024);
@@ -1610,7 +1834,6 @@ gtls_status ensure_chunk(gtls_plan* pl)
     DevChunk& dk = pl->dk;
     const int64_t chunk = dk.chunk;
     GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.fold_stride));
-    GTLS_TRY(dev_alloc(pl, &dk.slot, chunk * dk.fold_stride));
     GTLS_TRY(dev_alloc(pl, &dk.sidx, chunk * dk.fold_stride));
     GTLS_TRY(dev_alloc(pl, &dk.rs, chunk * dk.pad_stride));
     GTLS_TRY(dev_alloc(pl, &dk.ws, chunk * dk.pad_stride));
@@ -2282,7 +2505,7 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     DevChunk& dk = b->dk;
     dk.fold_stride = fold_stride;
     dk.pad_stride = pad_stride;
-    const int64_t per_slot = fold_stride * (8 + 4 + 4) + pad_stride * (4 + 4 + 4 + 8);
+    const int64_t per_slot = fold_stride * (8 + 4) + pad_stride * (4 + 4 + 4 + 8);
     const int64_t budget = int64_t(8) << 30;
     int64_t slots = std::min<int64_t>(4096, std::max<int64_t>(1, budget / per_slot));
     if (wave_slots > 0) slots = wave_slots;
@@ -2290,7 +2513,6 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     b->cfg.wave_slots = (int)slots;
     dk.chunk = (int32_t)slots;
     GTLS_TRY(batch_alloc(b, &dk.keys, slots * fold_stride));
-    GTLS_TRY(batch_alloc(b, &dk.slot, slots * fold_stride));
     GTLS_TRY(batch_alloc(b, &dk.sidx, slots * fold_stride));
     GTLS_TRY(batch_alloc(b, &dk.rs, slots * pad_stride));
     GTLS_TRY(batch_alloc(b, &dk.ws, slots * pad_stride));

@@ -304,13 +304,17 @@ def test_kepler_like_per_point_weights_sampled_parity():
 def test_phase_pile_up_takes_the_global_memory_fold():
     # 20,000 points one day apart: at trial periods of 0.5, 1 and 2 days every
     # point shares one or two phases, so single buckets hold 10,000-20,000
-    # keys (beyond one shared-memory run); other periods spread them
+    # keys (beyond one shared-memory run); at 2.00001 days two clusters of
+    # 10,000 points spread over 5 % of the phase each (a super-bucket too full
+    # for shared memory, made of buckets that are not); at 3 and 7.3 days
+    # the staged fold meets fine buckets of 6,667 and 274 equal phases;
+    # other periods spread the points
     n = 20000
     t = np.arange(n, dtype=np.float64)
     rng = np.random.default_rng(4)
     y = 1.0 + rng.normal(0, 1e-3, n)
     dy = np.full(n, 1e-3)
-    periods = np.array([0.5, 1.0, 2.0, 3.0, 0.77123, 1.5, 7.3])
+    periods = np.array([0.5, 1.0, 2.0, 2.00001, 3.0, 0.77123, 1.5, 7.3])
     base = float(t[-1] - t[0])
     op = gh.oracle_plan_for(n, base, periods_days=periods)
     r_or = osr.search_periods(op, t, y, dy)
