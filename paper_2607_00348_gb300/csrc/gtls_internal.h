@@ -68,8 +68,9 @@ struct DevCurve {
 struct DevChunk {
     int32_t chunk;
     int64_t fold_stride;      // >= n
+    int64_t key_stride;       // >= n and >= the super-bucket regions of the fold
     int64_t pad_stride;       // >= n + dmax + margin (folded, padded arrays)
-    unsigned long long* keys; // bucket-ordered fold keys
+    unsigned long long* keys; // fold keys (super-bucket regions, or bucket order)
     int32_t* sidx;            // folded order -> original index
     float* rs;                // folded r, padded by the period's first D_m points
     float* ws;                // folded w (per-point weights only)

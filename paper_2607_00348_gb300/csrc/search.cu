@@ -123,6 +123,13 @@ __device__ __forceinline__ bool in_range(unsigned int* w, unsigned int code, lon
     return false;
 }
 
+__device__ __forceinline__ bool in_range32(unsigned int* w, unsigned int code, uint32_t v, uint32_t hi)
+{
+    if (v < hi) return true;
+    record_check(w, code, v, hi);
+    return false;
+}
+
 // Exact lattice phase rho = d mod P (0 <= d < 2^62, P > 0).  The float
 // product gives the cycle count to within one; two integer corrections make
 // it exact.
@@ -314,13 +321,13 @@ __global__ void k_curve_reduce(const double* __restrict__ dy, const int64_t* __r
 // into 2^sb_log2 super-buckets of 2^kFoldFineLog2 each).
 //
 // Staged path (the common case): the keys are scattered once into global
-// memory in super-bucket order -- a few dozen write streams that fill whole
-// cache lines -- and every super-bucket (at most kFoldSegKeys keys) is then
-// bucket sorted, ranked, gathered and scanned in shared memory.  Global path
-// (a phase pile-up: some super-bucket too full for shared memory): the keys
-// are scattered into global memory in bucket order and runs of whole buckets
-// are ranked and scanned (in shared memory while a run fits, else in global
-// memory).
+// memory, each into its super-bucket's region of kFoldSegKeys slots -- a few
+// dozen write streams that fill whole cache lines -- and every super-bucket
+// is then bucket sorted, ranked, gathered and scanned in shared memory.
+// Global path (a phase pile-up: some super-bucket too full for its region):
+// the keys are scattered into global memory in bucket order and runs of
+// whole buckets are ranked and scanned (in shared memory while a run fits,
+// else in global memory).
 
 constexpr int kFoldFineLog2 = 11;   // fine buckets per super-bucket (log2)
 constexpr int kFoldMaxSbLog2 = 10;  // at most one super-bucket per fold thread
@@ -355,9 +362,9 @@ struct FoldOut {
 
 // Rank keys[q] (q < len, staged in shared memory in bucket order) inside
 // their buckets, gather the folded curve into positions k0 + rank of the
-// outputs and the folded rfx into srfx[rank].  bucket_of(key, b) gives the
-// bucket b (false: skip the key); its keys occupy [e - cnt_of[b], e) of keys
-// with e = end_of[b] - end_base.
+// outputs and the folded rfx into srfx[rank].  bucket_of(q, key, b) gives the
+// bucket b of keys[q] (false: skip the key); its keys occupy
+// [e - cnt_of[b], e) of keys with e = end_of[b] - end_base.
 template <typename BucketOf>
 __device__ __forceinline__ void fold_rank_gather(const unsigned long long* keys, uint32_t len, uint32_t k0,
                                                  const uint32_t* cnt_of, const uint32_t* end_of,
@@ -377,13 +384,15 @@ __device__ __forceinline__ void fold_rank_gather(const unsigned long long* keys,
             if (q >= len) continue;
             const unsigned long long key = keys[q];
             int b;
-            if (!bucket_of(key, b)) continue;
-            const uint32_t cnt = cnt_of[b], lo = end_of[b] - end_base - cnt;
-            if (!in_range(dc.check, 6, (long long)lo + cnt, (long long)len + 1)) continue;
+            if (!bucket_of(q, key, b)) continue;
+            const uint32_t cnt = cnt_of[b], e = end_of[b] - end_base;
+            if (!in_range32(dc.check, 6, e, len + 1) || !in_range32(dc.check, 6, cnt, e + 1)) continue;
+            const uint32_t lo = e - cnt;
             uint32_t rank = 0;
             for (uint32_t u = 0; u < cnt; ++u) rank += keys[lo + u] < key ? 1u : 0u;
             const int32_t id = (int32_t)(key & idx_mask);
-            if (!in_range(dc.check, 7, lo + rank, len) || !in_range(dc.check, 8, id, n)) continue;
+            if (!in_range32(dc.check, 7, lo + rank, len) || !in_range32(dc.check, 8, (uint32_t)id, (uint32_t)n))
+                continue;
             pos[j] = lo + rank;
             idx[j] = id;
         }
@@ -432,8 +441,8 @@ __device__ __forceinline__ void fold_scan_run(const long long* srfx, uint32_t le
     }
 }
 
-// Staged path; false (nothing written) when a super-bucket holds more than
-// kFoldSegKeys points.
+// Staged path; false when a super-bucket holds more than kFoldSegKeys
+// points (only keys have been written then).
 __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCurve& dc, int p,
                             unsigned long long* keys, const FoldOut& o)
 {
@@ -450,6 +459,7 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     constexpr uint32_t kFineMask = (1u << kFoldFineLog2) - 1u;
     static_assert((1 << kFoldFineLog2) % kFoldThreads == 0, "fine buckets split evenly over the threads");
     static_assert((1 << kFoldMaxSbLog2) <= kFoldThreads, "one super-bucket count per thread");
+    static_assert(kFoldFineLog2 <= 16, "fine bucket indices are kept as 16-bit values");
 
     long long* warp_sums = reinterpret_cast<long long*>(smem);
     long long* total = warp_sums + 32;
@@ -459,56 +469,52 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     uint32_t* fcur = fcnt + (1 << kFoldFineLog2);
     uint32_t* sb_cnt = fcur + (1 << kFoldFineLog2);
     uint32_t* sb_start = sb_cnt + (1 << kFoldMaxSbLog2);
-    uint32_t* sb_cur = sb_start + (1 << kFoldMaxSbLog2);
-    int* overflow = reinterpret_cast<int*>(sb_cur + (1 << kFoldMaxSbLog2));
+    uint16_t* stage_f = reinterpret_cast<uint16_t*>(sb_start + (1 << kFoldMaxSbLog2));   // fine bucket of stage[q]
+    uint16_t* sorted_f = stage_f + kFoldSegKeys;                                          // of sorted[q]
+    int* overflow = reinterpret_cast<int*>(sorted_f + kFoldSegKeys);
 
     for (int q = threadIdx.x; q < nsb; q += blockDim.x) sb_cnt[q] = 0;
     if (threadIdx.x == 0) *overflow = 0;
     __syncthreads();
 
-    // A. super-bucket of every point: counts, then the scatter (the loop
-    // bounds are block-uniform so that whole warps take the aggregated
-    // increments)
+    // A. super-bucket of every point; its key goes to the next slot of the
+    // super-bucket's region (the loop bounds are block-uniform so that whole
+    // warps take the aggregated increments)
     const int64_t bs = blockDim.x;
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int64_t g0 = 0; g0 < n; g0 += kFoldUnroll * bs) {
-            long long dl[kFoldUnroll];
-            float df[kFoldUnroll];
+    for (int64_t g0 = 0; g0 < n; g0 += kFoldUnroll * bs) {
+        long long dl[kFoldUnroll];
+        float df[kFoldUnroll];
 #pragma unroll
-            for (int u = 0; u < kFoldUnroll; ++u) {
-                const int64_t i = g0 + u * bs + threadIdx.x;
-                dl[u] = i < n ? dc.d_lat[i] : 0;
-                df[u] = i < n ? dc.d_f[i] : 0.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < kFoldUnroll; ++u) {
-                const int64_t i = g0 + u * bs + threadIdx.x;
-                const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
-                const uint32_t sb = fold_fine(rho, sh, mul, fshift) >> kFoldFineLog2;
-                const bool ok = i < n && in_range(dc.check, 2, rho, P) && in_range(dc.check, 1, sb, nsb);
-                const unsigned int active = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    const uint32_t slot = agg_slot(pass == 0 ? sb_cnt : sb_cur, sb, active);
-                    if (pass == 1 && in_range(dc.check, 4, slot, n))
-                        keys[slot] = ((unsigned long long)rho << ib) | (unsigned long long)i;
-                }
-            }
+        for (int u = 0; u < kFoldUnroll; ++u) {
+            const int64_t i = g0 + u * bs + threadIdx.x;
+            dl[u] = i < n ? dc.d_lat[i] : 0;
+            df[u] = i < n ? dc.d_f[i] : 0.0f;
         }
-        __syncthreads();
-        if (pass == 0) {
-            // super-bucket starts; any super-bucket too large for shared
-            // memory sends the period to the global path
-            const uint32_t c = threadIdx.x < nsb ? sb_cnt[threadIdx.x] : 0u;
-            if (c > (uint32_t)kFoldSegKeys) *overflow = 1;
-            const long long st = block_exclusive_scan(c, warp_sums, total);
-            if (threadIdx.x < nsb) {
-                sb_start[threadIdx.x] = (uint32_t)st;
-                sb_cur[threadIdx.x] = (uint32_t)st;
+#pragma unroll
+        for (int u = 0; u < kFoldUnroll; ++u) {
+            const int64_t i = g0 + u * bs + threadIdx.x;
+            const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
+            const uint32_t sb = fold_fine(rho, sh, mul, fshift) >> kFoldFineLog2;
+            const bool ok = i < n && in_range(dc.check, 2, rho, P) && in_range32(dc.check, 1, sb, nsb);
+            const unsigned int active = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const uint32_t slot = agg_slot(sb_cnt, sb, active);
+                if (slot < (uint32_t)kFoldSegKeys)
+                    keys[(int64_t)sb * kFoldSegKeys + slot] = ((unsigned long long)rho << ib) | (unsigned long long)i;
+                else
+                    *overflow = 1;
             }
-            __syncthreads();
-            if (*overflow) return false;
         }
     }
+    __syncthreads();
+    if (*overflow) return false;
+    {
+        // positions of the super-buckets in the folded order
+        const uint32_t c = threadIdx.x < nsb ? sb_cnt[threadIdx.x] : 0u;
+        const long long st = block_exclusive_scan(c, warp_sums, total);
+        if (threadIdx.x < nsb) sb_start[threadIdx.x] = (uint32_t)st;
+    }
+    __syncthreads();
 
     // B. each super-bucket in shared memory
     long long carry = 0;
@@ -516,12 +522,15 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     for (int sb = 0; sb < nsb; ++sb) {
         const uint32_t k0 = sb_start[sb], len = sb_cnt[sb];
         if (len == 0) continue;
+        const unsigned long long* region = keys + (int64_t)sb * kFoldSegKeys;
         for (int f = threadIdx.x; f < (1 << kFoldFineLog2); f += blockDim.x) fcnt[f] = 0;
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
-            const unsigned long long key = keys[k0 + q];
+            const unsigned long long key = region[q];
+            const uint32_t f = fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask;
             stage[q] = key;
-            atomicAdd(&fcnt[fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask], 1u);
+            stage_f[q] = (uint16_t)f;
+            atomicAdd(&fcnt[f], 1u);
         }
         __syncthreads();
         {
@@ -539,15 +548,17 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
         }
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
-            const unsigned long long key = stage[q];
-            const uint32_t f = fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask;
+            const uint32_t f = stage_f[q];
             const uint32_t d = atomicAdd(&fcur[f], 1u);   // fcur[f] ends as the end of bucket f
-            if (in_range(dc.check, 5, d, len)) sorted[d] = key;
+            if (in_range32(dc.check, 5, d, len)) {
+                sorted[d] = stage[q];
+                sorted_f[d] = (uint16_t)f;
+            }
         }
         __syncthreads();
         long long* srfx = reinterpret_cast<long long*>(stage);
-        auto bucket_of = [&](unsigned long long key, int& f) {
-            f = (int)(fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask);
+        auto bucket_of = [&](uint32_t q, unsigned long long, int& f) {
+            f = sorted_f[q];
             return true;
         };
         fold_rank_gather(sorted, len, k0, fcnt, fcur, 0u, bucket_of, ib, idx_mask, n, dc, o, srfx);
@@ -671,7 +682,7 @@ __device__ void fold_global(unsigned char* smem, const DevPlan& dp, const DevCur
         if (len <= (uint32_t)kFoldSegKeys) {
             for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) skeys[q] = keys[k0 + q];
             __syncthreads();
-            auto bucket_of = [&](unsigned long long key, int& b) {
+            auto bucket_of = [&](uint32_t, unsigned long long key, int& b) {
                 b = (int)fold_bucket((long long)(key >> ib), sh, mul);
                 return in_range(dc.check, 5, (long long)b - b_lo, b_hi - b_lo);
             };
@@ -728,7 +739,7 @@ k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
     const int slot_id = blockIdx.x;
     int lc, p;
     if (!resolve_slot(ds, sm, slot_id, lc, p)) return;
-    unsigned long long* const keys = dk.keys + (int64_t)slot_id * dk.fold_stride;
+    unsigned long long* const keys = dk.keys + (int64_t)slot_id * dk.key_stride;
     const DevPlan& dp = ds.plans[lc];
     const DevCurve dc = ds.curves[lc];
     FoldOut o;
@@ -1469,10 +1480,12 @@ int fold_smem_bytes(int bucket_log2)
     const int global_path = (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long) +
                             kFoldSegKeys * (int)(sizeof(unsigned long long) + sizeof(long long));
     // staged path: scan scratch, staged and sorted keys, fine-bucket counts
-    // and ends, super-bucket counts, starts and cursors, overflow flag
+    // and ends, super-bucket counts and starts, fine buckets of the staged
+    // and sorted keys, overflow flag
     const int staged = 33 * (int)sizeof(long long) + 2 * kFoldSegKeys * (int)sizeof(unsigned long long) +
                        (2 << kFoldFineLog2) * (int)sizeof(uint32_t) +
-                       3 * (1 << kFoldMaxSbLog2) * (int)sizeof(uint32_t) + (int)sizeof(int);
+                       2 * (1 << kFoldMaxSbLog2) * (int)sizeof(uint32_t) +
+                       2 * kFoldSegKeys * (int)sizeof(uint16_t) + (int)sizeof(int);
     return std::max(global_path, staged);
 }
 
@@ -1587,9 +1600,10 @@ gtls_status create_device(gtls_plan* pl)
 
     DevChunk& dk = pl->dk;
     dk.fold_stride = (n + 31) & ~int64_t(31);
+    dk.key_stride = std::max<int64_t>(dk.fold_stride, (int64_t)kFoldSegKeys << dp.fold_sb_log2);
     dk.pad_stride = (n + h.dmax + kPadMargin + 31) & ~int64_t(31);
-    const int64_t per_period = dk.fold_stride * (8 + 4) + dk.pad_stride * (4 + 4 + 4 + 8);
-    const int64_t budget = int64_t(1) << 31;  // 2 GiB of chunk scratch
+    const int64_t per_period = dk.key_stride * 8 + dk.fold_stride * 4 + dk.pad_stride * (4 + 4 + 4 + 8);
+    const int64_t budget = int64_t(3) << 30;  // 3 GiB of chunk scratch
     int64_t chunk = std::max<int64_t>(1, budget / per_period);
     chunk = std::min<int64_t>(chunk, 1024);
     if (h.prm.periods_per_chunk > 0) chunk = h.prm.periods_per_chunk;
@@ -1833,7 +1847,7 @@ gtls_status ensure_chunk(gtls_plan* pl)
     if (pl->chunk_ready) return GTLS_OK;
     DevChunk& dk = pl->dk;
     const int64_t chunk = dk.chunk;
-    GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.fold_stride));
+    GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.key_stride));
     GTLS_TRY(dev_alloc(pl, &dk.sidx, chunk * dk.fold_stride));
     GTLS_TRY(dev_alloc(pl, &dk.rs, chunk * dk.pad_stride));
     GTLS_TRY(dev_alloc(pl, &dk.ws, chunk * dk.pad_stride));
@@ -2464,7 +2478,7 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     b->plans.assign(plans, plans + n_lc);
     b->off.assign(1, 0);
     int bucket_log2 = 0, max_np_blocks = 1, topk = 0, buf_max = 1 << 30;
-    int64_t fold_stride = 32, pad_stride = 32;
+    int64_t fold_stride = 32, key_stride = 32, pad_stride = 32;
     bool any_tiled = false;
     for (int i = 0; i < b->n_lc; ++i) {
         gtls_plan* pl = plans[i];
@@ -2478,6 +2492,7 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
         b->max_kept = std::max(b->max_kept, h.max_kept);
         bucket_log2 = std::max(bucket_log2, h.bucket_log2);
         fold_stride = std::max<int64_t>(fold_stride, pl->dk.fold_stride);
+        key_stride = std::max<int64_t>(key_stride, pl->dk.key_stride);
         pad_stride = std::max<int64_t>(pad_stride, pl->dk.pad_stride);
         const int mo = median_outs(pl->dp.median_half);
         max_np_blocks = std::max(max_np_blocks, (pl->dp.np + mo - 1) / mo);
@@ -2504,15 +2519,16 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     // chunk scratch shared by all curves: slots of the largest curve's strides
     DevChunk& dk = b->dk;
     dk.fold_stride = fold_stride;
+    dk.key_stride = key_stride;
     dk.pad_stride = pad_stride;
-    const int64_t per_slot = fold_stride * (8 + 4) + pad_stride * (4 + 4 + 4 + 8);
+    const int64_t per_slot = key_stride * 8 + fold_stride * 4 + pad_stride * (4 + 4 + 4 + 8);
     const int64_t budget = int64_t(8) << 30;
     int64_t slots = std::min<int64_t>(4096, std::max<int64_t>(1, budget / per_slot));
     if (wave_slots > 0) slots = wave_slots;
     b->max_slots = (int)slots;
     b->cfg.wave_slots = (int)slots;
     dk.chunk = (int32_t)slots;
-    GTLS_TRY(batch_alloc(b, &dk.keys, slots * fold_stride));
+    GTLS_TRY(batch_alloc(b, &dk.keys, slots * key_stride));
     GTLS_TRY(batch_alloc(b, &dk.sidx, slots * fold_stride));
     GTLS_TRY(batch_alloc(b, &dk.rs, slots * pad_stride));
     GTLS_TRY(batch_alloc(b, &dk.ws, slots * pad_stride));
