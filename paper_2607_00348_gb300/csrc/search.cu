@@ -516,7 +516,20 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     }
     __syncthreads();
 
-    // B. each super-bucket in shared memory
+    // B. each super-bucket in shared memory: the keys staged with their fine
+    // bucket, counting-sorted by fine bucket and ranked inside it, which
+    // gives inv[final position] = sorted position; then, in final-position
+    // order, the folded curve gathered (coalesced stores), rfx scanned and
+    // the prefix sums written.
+    constexpr int kPerThread = kFoldSegKeys / kFoldThreads;
+    static_assert(kFoldSegKeys % kFoldThreads == 0, "staged keys split evenly over the threads");
+    static_assert(kPerThread == kScanPer, "one scan pass per super-bucket");
+    static_assert(kPerThread % kRankBatch == 0, "gathers issued in whole batches");
+    uint16_t* const inv = stage_f;                                     // reused after the scatter
+    long long* const srfx = reinterpret_cast<long long*>(stage);       // reused after the scatter
+    // srfx is read in blocks of kScanPer consecutive entries per thread; the
+    // swizzle spreads the 16 lanes of a half-warp over 16 bank pairs
+    auto swz = [](uint32_t i) { return i ^ ((i >> 4) & 7u); };
     long long carry = 0;
     if (threadIdx.x == 0) o.pf[0] = 0;
     for (int sb = 0; sb < nsb; ++sb) {
@@ -525,12 +538,22 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
         const unsigned long long* region = keys + (int64_t)sb * kFoldSegKeys;
         for (int f = threadIdx.x; f < (1 << kFoldFineLog2); f += blockDim.x) fcnt[f] = 0;
         __syncthreads();
-        for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
-            const unsigned long long key = region[q];
-            const uint32_t f = fold_fine((long long)(key >> ib), sh, mul, fshift) & kFineMask;
-            stage[q] = key;
-            stage_f[q] = (uint16_t)f;
-            atomicAdd(&fcnt[f], 1u);
+        {
+            unsigned long long kv[kPerThread];
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const uint32_t q = threadIdx.x + u * kFoldThreads;
+                kv[u] = q < len ? region[q] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const uint32_t q = threadIdx.x + u * kFoldThreads;
+                if (q >= len) break;
+                const uint32_t f = fold_fine((long long)(kv[u] >> ib), sh, mul, fshift) & kFineMask;
+                stage[q] = kv[u];
+                stage_f[q] = (uint16_t)f;
+                atomicAdd(&fcnt[f], 1u);
+            }
         }
         __syncthreads();
         {
@@ -556,14 +579,76 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             }
         }
         __syncthreads();
-        long long* srfx = reinterpret_cast<long long*>(stage);
-        auto bucket_of = [&](uint32_t q, unsigned long long, int& f) {
-            f = sorted_f[q];
-            return true;
-        };
-        fold_rank_gather(sorted, len, k0, fcnt, fcur, 0u, bucket_of, ib, idx_mask, n, dc, o, srfx);
+        // rank inside the fine bucket: [fcur[f] - fcnt[f], fcur[f]) of sorted
+        for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
+            const unsigned long long key = sorted[q];
+            const uint32_t f = sorted_f[q];
+            const uint32_t cnt = fcnt[f], e = fcur[f];
+            if (!in_range32(dc.check, 6, e, len + 1) || !in_range32(dc.check, 6, cnt, e + 1)) continue;
+            const uint32_t lo = e - cnt;
+            uint32_t rank = 0;
+            for (uint32_t u = 0; u < cnt; ++u) rank += sorted[lo + u] < key ? 1u : 0u;
+            if (in_range32(dc.check, 7, lo + rank, len)) inv[lo + rank] = (uint16_t)q;
+        }
         __syncthreads();
-        fold_scan_run(srfx, len, k0, o.pf, carry, warp_sums, total);
+        // gather in final-position order (kRankBatch points' loads in flight)
+#pragma unroll
+        for (int h = 0; h < kPerThread; h += kRankBatch) {
+            int32_t id[kRankBatch];
+            bool ok[kRankBatch];
+#pragma unroll
+            for (int j = 0; j < kRankBatch; ++j) {
+                const uint32_t i = threadIdx.x + (h + j) * kFoldThreads;
+                ok[j] = false;
+                id[j] = 0;
+                if (i >= len) continue;
+                const uint32_t q = inv[i];
+                if (!in_range32(dc.check, 7, q, len)) continue;
+                id[j] = (int32_t)(sorted[q] & idx_mask);
+                ok[j] = in_range32(dc.check, 8, (uint32_t)id[j], (uint32_t)n);
+            }
+            float rv[kRankBatch];
+            long long fv[kRankBatch];
+#pragma unroll
+            for (int j = 0; j < kRankBatch; ++j) {
+                rv[j] = ok[j] ? dc.r32[id[j]] : 0.0f;
+                fv[j] = ok[j] ? dc.rfx[id[j]] : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kRankBatch; ++j) {
+                const uint32_t i = threadIdx.x + (h + j) * kFoldThreads;
+                if (!ok[j]) continue;
+                const int64_t g = (int64_t)k0 + i;
+                o.sidx[g] = id[j];
+                o.rs[g] = rv[j];
+                srfx[swz(i)] = fv[j];
+                if (!o.uniform) {
+                    const float w = dc.w32[id[j]];
+                    o.ws[g] = w;
+                    o.wrs[g] = w * rv[j];
+                }
+            }
+        }
+        __syncthreads();
+        // inclusive prefix of rfx in final order, kScanPer consecutive
+        // entries per thread, written back in place
+        {
+            const uint32_t i0 = threadIdx.x * kScanPer;
+            long long v[kScanPer];
+            long long run = 0;
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) {
+                run += i0 + u < len ? srfx[swz(i0 + u)] : 0;
+                v[u] = run;
+            }
+            const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u)
+                if (i0 + u < len) srfx[swz(i0 + u)] = ex + v[u];
+            carry += *total;
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) o.pf[(int64_t)k0 + 1 + i] = srfx[swz(i)];
         __syncthreads();   // the next super-bucket overwrites the staged keys and rfx
     }
     return true;
