@@ -1502,18 +1502,26 @@ gtls_status upload(gtls_plan* pl, T** ptr, const std::vector<T>& v)
         if (s_ != GTLS_OK) return s_;   \
     } while (0)
 
-// Window-kernel variant and phase lanes for a T0 step st with about `nwin`
-// windows per tile: the candidates keep W st = nc * odd (mod 32) (bank
-// conflict free); the score is the useful fraction of lane slots times an
-// issue-rate factor of the variant.
-void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
+// Window-kernel variant and phase lanes for a duration of d points, T0 step
+// st and about `nwin` windows per tile: the candidates keep W st = nc * odd
+// (mod 32) (bank conflict free); the one with the lowest predicted time per
+// window-point evaluation wins.  Predicted time = intrinsic cost of the
+// variant / (useful fraction of lane slots x filled fraction of the last
+// task x share of a window's time spent on its points).  The intrinsic
+// costs are warp cycles per issued FMA lane measured on the Kepler-like
+// search (clock64 around every task): 15-window column pairs 250, 16-window
+// 272, 12-window 344, window pairs 348; the (C1, S) pairs spend two lanes
+// per evaluation but finish a window without prefix-sum reads.  A window's
+// epilogue (reduction, two 8-byte prefix reads, the packed minimum) costs
+// about as much as 80 evaluations (about 20 for the (C1, S) pairs).
+void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out)
 {
     int v = 0;
     while (v < 5 && ((st >> v) & 1) == 0) ++v;
-    double best = -1.0;
+    double best = 1e300;
     variant = tiles::kWin16;
     nc_out = 32;
-    auto consider = [&](int var, int nc, double ipc) {
+    auto consider = [&](int var, int nc) {
         if (nc > 32 || nc < 1) return;
         const int w = tiles::variant_w(var);
         const int cols = tiles::variant_colpair(var) ? 2 * nc : nc;
@@ -1522,41 +1530,31 @@ void pick_config_host(int st, int nwin, int32_t& variant, int32_t& nc_out)
         const int per = 32 * w / nc;
         const int tasks = (nwin + per - 1) / per;
         const double fill = (double)nwin / (double)(tasks * per);
-        const double eff = util * fill * ipc;
-        if (eff > best + 1e-9) {
-            best = eff;
+        double base, epi;
+        switch (var) {
+        case tiles::kCol15: base = 250.0; epi = 80.0; break;
+        case tiles::kCol16: base = 272.0; epi = 80.0; break;
+        case tiles::kCol12: base = 344.0; epi = 80.0; break;
+        case tiles::kWin16: base = 348.0; epi = 80.0; break;
+        default: base = 2.0 * 240.0; epi = 20.0; break;   // (C1, S) pairs: two lanes per evaluation
+        }
+        const double cost = base / (util * fill * ((double)d / (d + epi)));
+        if (cost < best - 1e-9) {
+            best = cost;
             variant = var;
             nc_out = nc;
         }
     };
-    // issue-rate factor: min(1, 0.85 x FMA-pipe cycles / issue slots per row);
-    // a row costs the variant's FFMA(2)s plus ~7 (winpair), ~6 (colpair) or
-    // ~5 (scalar) other instructions
-    auto ipc = [](int var) {
-        const int w = tiles::variant_w(var);
-        double pipe, slots;
-        if (var == tiles::kScalar15) {
-            pipe = w;            // half of the FFMA2 work is the window sum S
-            slots = w + 6;
-        } else if (tiles::variant_colpair(var)) {
-            pipe = 2.0 * w;
-            slots = w + 6;
-        } else {
-            pipe = w;
-            slots = w / 2 + 7;
-        }
-        return std::min(1.0, 0.85 * pipe / slots);
-    };
     // variants built into the kernel: scalar15 (nc = 2^v), winpair16 (nc = 32),
     // colpair 16 / 15 / 12 (W st = nc * odd)
-    consider(tiles::kWin16, 32, ipc(tiles::kWin16));
-    consider(tiles::kCol16, 32, ipc(tiles::kCol16));
+    consider(tiles::kWin16, 32);
+    consider(tiles::kCol16, 32);
     if (v <= 4) {
-        consider(tiles::kScalar15, 1 << v, ipc(tiles::kScalar15));
-        consider(tiles::kCol15, 1 << v, ipc(tiles::kCol15));
+        consider(tiles::kScalar15, 1 << v);
+        consider(tiles::kCol15, 1 << v);
     }
-    if (v + 2 <= 5) consider(tiles::kCol12, 1 << (v + 2), ipc(tiles::kCol12));
-    if (v + 4 <= 5) consider(tiles::kCol16, 1 << (v + 4), ipc(tiles::kCol16));
+    if (v + 2 <= 5) consider(tiles::kCol12, 1 << (v + 2));
+    if (v + 4 <= 5) consider(tiles::kCol16, 1 << (v + 4));
 }
 
 int fold_smem_bytes(int bucket_log2)
@@ -1764,7 +1762,7 @@ gtls_status create_device(gtls_plan* pl)
                 const int st = h.stride[j];
                 const int64_t m_total = (n + st - 1) / st;
                 const int nwin = (int)std::min<int64_t>(m_total, (len + st - 1) / st);
-                pick_config_host(st, nwin, var[j], ncs[j]);
+                pick_config_host(h.dpts[j], st, nwin, var[j], ncs[j]);
                 if (!fit[j]) {
                     var[j] = tiles::kWindowOnly;
                     ncs[j] = 32;
