@@ -944,7 +944,7 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
     using namespace tiles;
     extern __shared__ float tile_smem[];
     __shared__ DurTask dur[kMaxDur];
-    __shared__ int s_item, s_ndur, s_total, s_task, s_lc, s_p, s_slot, s_x0, s_len;
+    __shared__ int s_item, s_ndur, s_total, s_task, s_lc, s_p, s_slot, s_x0, s_len, s_tau, s_tcount;
     __shared__ unsigned long long s_best[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
@@ -967,12 +967,14 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
                 s_slot = sm.seg[g].slot0 + k;
                 s_x0 = tau * (weighted ? tl.len_w : tl.len);
                 s_len = weighted ? tl.len_w : tl.len;
+                s_tau = tau;
+                s_tcount = tcount;
             }
         }
         __syncthreads();
         const int item = s_item;
         if (item >= sm.items) break;
-        const int lc = s_lc, p = s_p, slot = s_slot, x0 = s_x0, tile_len = s_len;
+        const int lc = s_lc, p = s_p, slot = s_slot, x0 = s_x0, tile_len = s_len, tau = s_tau, tcount = s_tcount;
         if (p < 0) {   // block-uniform: a failed check skips the item
             __syncthreads();
             continue;
@@ -1018,13 +1020,31 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
                     t.m_total = (int)((n + t.st - 1) / t.st);
                     t.m_a = (x0 + t.st - 1) / t.st;
                     t.m_b = min(t.m_total, (x0 + tile_len + t.st - 1) / t.st);
-                    const int nwin = max(0, t.m_b - t.m_a);
                     t.variant = weighted ? (int)kWeighted15 : dp.cfg_variant[j];
                     t.nc = weighted ? dp.cfg_nc_w[j] : dp.cfg_nc[j];
                     t.w = variant_w(t.variant);
                     t.per_task = 32 * t.w / t.nc;
-                    t.tasks = (!weighted && t.variant == kWindowOnly) ? 0 : (nwin + t.per_task - 1) / t.per_task;
                     const int jrows = (t.d + t.st - 1) / t.st;
+                    {
+                        // whole tasks per tile where the staged buffers have room:
+                        // the duration covers windows [tau K, (tau + 1) K) of tile
+                        // tau, K a multiple of the task length with K st >= L (each
+                        // tile starts inside its buffer) and K st <= L + room /
+                        // tiles (the last tile's blocks and rows still fit), so
+                        // that only its last tile has a partly filled task
+                        const long long room =
+                            (long long)buf - 32 - (long long)(jrows + t.w) * t.st - tile_len;
+                        if (room > 0) {
+                            const long long span = tile_len + room / tcount;
+                            const long long k = span / t.st / t.per_task * t.per_task;
+                            if (k * t.st >= tile_len) {
+                                t.m_a = (int)min((long long)t.m_total, (long long)tau * k);
+                                t.m_b = (int)min((long long)t.m_total, (long long)(tau + 1) * k);
+                            }
+                        }
+                    }
+                    const int nwin = max(0, t.m_b - t.m_a);
+                    t.tasks = (!weighted && t.variant == kWindowOnly) ? 0 : (nwin + t.per_task - 1) / t.per_task;
                     t.jrows = jrows;
                     t.tg = dp.tmpl + dp.tmpl_off[j];
                     t.tg2 = weighted ? dp.tmplw + dp.tmplw_off[j] : dp.tmpl2 + dp.tmpl2_off[j];
