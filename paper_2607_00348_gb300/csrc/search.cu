@@ -337,20 +337,6 @@ __device__ __forceinline__ uint32_t fold_fine(long long rho, int sh, uint32_t mu
     return (uint32_t)((((unsigned long long)rho >> sh) * (unsigned long long)mul) >> fshift);
 }
 
-// Warp-aggregated increment of cnt[s] by one per lane of `active` (the lanes
-// calling it): returns the lane's slot, i.e. the counter's value before the
-// warp's increment plus the rank of the lane among lanes with the same s.
-__device__ __forceinline__ uint32_t agg_slot(uint32_t* cnt, uint32_t s, unsigned int active)
-{
-    const unsigned int peers = __match_any_sync(active, s);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&cnt[s], (uint32_t)__popc(peers));
-    base = __shfl_sync(active, base, leader);
-    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-}
-
 struct FoldOut {
     int32_t* sidx;
     float* rs;
@@ -478,8 +464,8 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     __syncthreads();
 
     // A. super-bucket of every point; its key goes to the next slot of the
-    // super-bucket's region (the loop bounds are block-uniform so that whole
-    // warps take the aggregated increments)
+    // super-bucket's region (a shared-memory atomic per point: aggregating
+    // the lanes of a warp with equal super-buckets first measured slower)
     const int64_t bs = blockDim.x;
     for (int64_t g0 = 0; g0 < n; g0 += kFoldUnroll * bs) {
         long long dl[kFoldUnroll];
@@ -496,9 +482,8 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
             const uint32_t sb = fold_fine(rho, sh, mul, fshift) >> kFoldFineLog2;
             const bool ok = i < n && in_range(dc.check, 2, rho, P) && in_range32(dc.check, 1, sb, nsb);
-            const unsigned int active = __ballot_sync(0xffffffffu, ok);
             if (ok) {
-                const uint32_t slot = agg_slot(sb_cnt, sb, active);
+                const uint32_t slot = atomicAdd(&sb_cnt[sb], 1u);
                 if (slot < (uint32_t)kFoldSegKeys)
                     keys[(int64_t)sb * kFoldSegKeys + slot] = ((unsigned long long)rho << ib) | (unsigned long long)i;
                 else
