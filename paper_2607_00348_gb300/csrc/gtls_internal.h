@@ -50,13 +50,18 @@ struct DevPlan {
     int32_t refine_k;           // periods re-searched with T0 step 1 (0: none)
 };
 
+// What the fold gathers for one point, in one 16-byte load.
+struct alignas(16) PointVals {
+    long long rfx;            // rint((1 - y) 2^40): exact window sums of r
+    float r;                  // float(1 - y)
+    float w;                  // float(1 / dy^2)
+};
+
 // Per-light-curve derived arrays (n long unless noted).
 struct DevCurve {
     int64_t* d_lat;           // rint((t - t_ref) 2^e)
     float* d_f;               // float(t - t_ref) (days): coarse cycle estimate
-    float* r32;               // float(1 - y)
-    long long* rfx;           // rint((1 - y) 2^40): exact window sums of r
-    float* w32;               // float(1 / dy^2)
+    PointVals* pv;            // rfx, r, w of every point
     double* scal;             // [0] t_ref [1] chi2_0 [2] uniform weight w (0 if not uniform)
     unsigned long long* tmin_key;  // ordered key of min(t)
     unsigned int* flags;      // bit0 non-finite, bit1 dy <= 0, bit2 dy not uniform

@@ -177,6 +177,32 @@ __device__ long long block_exclusive_scan(long long v, long long* warp_sums, lon
     return out;
 }
 
+// Exclusive scan of one long long per thread over the block with a single
+// barrier: every warp scans the warp totals itself.  `total` receives the
+// block sum.  The caller must pass a barrier before warp_sums is reused.
+__device__ long long block_exclusive_scan1(long long v, long long* warp_sums, long long& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    long long t = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+    }
+    total = __shfl_sync(0xffffffffu, t, 31);
+    const long long base = __shfl_sync(0xffffffffu, t, (warp + 31) & 31);   // inclusive sum of warps < warp
+    return (warp > 0 ? base : 0) + x - v;
+}
+
 // Light curve and period held by `slot` of a wave (segments ascend in
 // slot0); false when the period index is out of range.
 __device__ __forceinline__ bool resolve_slot(const DevSet& ds, const SlotMap& sm, int slot, int& lc, int& p)
@@ -275,9 +301,7 @@ __global__ void k_curve_prep(const double* __restrict__ t, const double* __restr
         const double w = 1.0 / (dy[i] * dy[i]);
         dc.d_lat[i] = __double2ll_rn(dt * scale);
         dc.d_f[i] = (float)dt;
-        dc.r32[i] = (float)r;
-        dc.rfx[i] = __double2ll_rn(r * kRScale);
-        dc.w32[i] = (float)w;
+        dc.pv[i] = PointVals{__double2ll_rn(r * kRScale), (float)r, (float)w};
         acc += w * r * r;
     }
 #pragma unroll
@@ -382,23 +406,20 @@ __device__ __forceinline__ void fold_rank_gather(const unsigned long long* keys,
             pos[j] = lo + rank;
             idx[j] = id;
         }
-        float rv[kRankBatch];
-        long long fv[kRankBatch];
+        PointVals pv[kRankBatch];
 #pragma unroll
-        for (int j = 0; j < kRankBatch; ++j) {
-            rv[j] = pos[j] != 0xffffffffu ? dc.r32[idx[j]] : 0.0f;
-            fv[j] = pos[j] != 0xffffffffu ? dc.rfx[idx[j]] : 0;
-        }
+        for (int j = 0; j < kRankBatch; ++j)
+            pv[j] = pos[j] != 0xffffffffu ? dc.pv[idx[j]] : PointVals{0, 0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < kRankBatch; ++j) {
             if (pos[j] == 0xffffffffu) continue;
             const int64_t g = (int64_t)k0 + pos[j];
             o.sidx[g] = idx[j];
-            o.rs[g] = rv[j];
-            srfx[pos[j]] = fv[j];
+            o.rs[g] = pv[j].r;
+            srfx[pos[j]] = pv[j].rfx;
             if (!o.uniform) {
-                o.ws[g] = dc.w32[idx[j]];
-                o.wrs[g] = dc.w32[idx[j]] * rv[j];
+                o.ws[g] = pv[j].w;
+                o.wrs[g] = pv[j].w * pv[j].r;
             }
         }
     }
@@ -547,7 +568,8 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             long long local = 0;
 #pragma unroll
             for (int u = 0; u < kPer; ++u) local += fcnt[f0 + u];
-            long long run = block_exclusive_scan(local, warp_sums, total);
+            long long sum;
+            long long run = block_exclusive_scan1(local, warp_sums, sum);
 #pragma unroll
             for (int u = 0; u < kPer; ++u) {
                 fcur[f0 + u] = (uint32_t)run;
@@ -592,25 +614,20 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
                 id[j] = (int32_t)(sorted[q] & idx_mask);
                 ok[j] = in_range32(dc.check, 8, (uint32_t)id[j], (uint32_t)n);
             }
-            float rv[kRankBatch];
-            long long fv[kRankBatch];
+            PointVals pv[kRankBatch];
 #pragma unroll
-            for (int j = 0; j < kRankBatch; ++j) {
-                rv[j] = ok[j] ? dc.r32[id[j]] : 0.0f;
-                fv[j] = ok[j] ? dc.rfx[id[j]] : 0;
-            }
+            for (int j = 0; j < kRankBatch; ++j) pv[j] = ok[j] ? dc.pv[id[j]] : PointVals{0, 0.0f, 0.0f};
 #pragma unroll
             for (int j = 0; j < kRankBatch; ++j) {
                 const uint32_t i = threadIdx.x + (h + j) * kFoldThreads;
                 if (!ok[j]) continue;
                 const int64_t g = (int64_t)k0 + i;
                 o.sidx[g] = id[j];
-                o.rs[g] = rv[j];
-                srfx[swz(i)] = fv[j];
+                o.rs[g] = pv[j].r;
+                srfx[swz(i)] = pv[j].rfx;
                 if (!o.uniform) {
-                    const float w = dc.w32[id[j]];
-                    o.ws[g] = w;
-                    o.wrs[g] = w * rv[j];
+                    o.ws[g] = pv[j].w;
+                    o.wrs[g] = pv[j].w * pv[j].r;
                 }
             }
         }
@@ -626,11 +643,12 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
                 run += i0 + u < len ? srfx[swz(i0 + u)] : 0;
                 v[u] = run;
             }
-            const long long ex = block_exclusive_scan(run, warp_sums, total) + carry;
+            long long sum;
+            const long long ex = block_exclusive_scan1(run, warp_sums, sum) + carry;
 #pragma unroll
             for (int u = 0; u < kScanPer; ++u)
                 if (i0 + u < len) srfx[swz(i0 + u)] = ex + v[u];
-            carry += *total;
+            carry += sum;
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) o.pf[(int64_t)k0 + 1 + i] = srfx[swz(i)];
@@ -772,12 +790,13 @@ __device__ void fold_global(unsigned char* smem, const DevPlan& dp, const DevCur
                 const uint32_t g = lo + rank;
                 const int32_t id = (int32_t)(key & idx_mask);
                 if (!in_range(dc.check, 7, g, n) || !in_range(dc.check, 8, id, n)) continue;
+                const PointVals v = dc.pv[id];
                 o.sidx[g] = id;
-                o.rs[g] = dc.r32[id];
-                o.pf[g + 1] = dc.rfx[id];
+                o.rs[g] = v.r;
+                o.pf[g + 1] = v.rfx;
                 if (!o.uniform) {
-                    o.ws[g] = dc.w32[id];
-                    o.wrs[g] = dc.w32[id] * dc.r32[id];
+                    o.ws[g] = v.w;
+                    o.wrs[g] = v.w * v.r;
                 }
             }
             __syncthreads();
@@ -1677,9 +1696,7 @@ gtls_status create_device(gtls_plan* pl)
     DevCurve& dc = pl->dc;
     GTLS_TRY(dev_alloc(pl, &dc.d_lat, n));
     GTLS_TRY(dev_alloc(pl, &dc.d_f, n));
-    GTLS_TRY(dev_alloc(pl, &dc.r32, n));
-    GTLS_TRY(dev_alloc(pl, &dc.rfx, n));
-    GTLS_TRY(dev_alloc(pl, &dc.w32, n));
+    GTLS_TRY(dev_alloc(pl, &dc.pv, n));
     GTLS_TRY(dev_alloc(pl, &dc.scal, 8));
     GTLS_TRY(dev_alloc(pl, &dc.tmin_key, 1));
     GTLS_TRY(dev_alloc(pl, &dc.flags, 1));
