@@ -1532,12 +1532,14 @@ gtls_status upload(gtls_plan* pl, T** ptr, const std::vector<T>& v)
 // window-point evaluation wins.  Predicted time = intrinsic cost of the
 // variant / (useful fraction of lane slots x filled fraction of the last
 // task x share of a window's time spent on its points).  The intrinsic
-// costs are warp cycles per issued FMA lane measured on the Kepler-like
-// search (clock64 around every task): 15-window column pairs 250, 16-window
-// 272, 12-window 344, window pairs 348; the (C1, S) pairs spend two lanes
-// per evaluation but finish a window without prefix-sum reads.  A window's
-// epilogue (reduction, two 8-byte prefix reads, the packed minimum) costs
-// about as much as 80 evaluations (about 20 for the (C1, S) pairs).
+// costs are warp cycles per 1000 issued FMA lanes, fitted to clock64
+// timings of every task of a Kepler-like search: 15-window column pairs
+// 220, 16-window 255, 12-window and window pairs 320; the (C1, S) pairs
+// spend two lanes per evaluation and their nc = st lanes per block a
+// recursive halving that grows with st (280 + 13 st per 1000 evaluations)
+// but finish a window without prefix-sum reads.  A window's epilogue
+// (reduction, two 8-byte prefix reads, the packed minimum) costs about as
+// much as 80 evaluations (about 20 for the (C1, S) pairs).
 void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out)
 {
     int v = 0;
@@ -1556,11 +1558,11 @@ void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out
         const double fill = (double)nwin / (double)(tasks * per);
         double base, epi;
         switch (var) {
-        case tiles::kCol15: base = 250.0; epi = 80.0; break;
-        case tiles::kCol16: base = 272.0; epi = 80.0; break;
-        case tiles::kCol12: base = 344.0; epi = 80.0; break;
-        case tiles::kWin16: base = 348.0; epi = 80.0; break;
-        default: base = 2.0 * 240.0; epi = 20.0; break;   // (C1, S) pairs: two lanes per evaluation
+        case tiles::kCol15: base = 220.0; epi = 80.0; break;
+        case tiles::kCol16: base = 255.0; epi = 80.0; break;
+        case tiles::kCol12: base = 320.0; epi = 80.0; break;
+        case tiles::kWin16: base = 320.0; epi = 80.0; break;
+        default: base = 280.0 + 13.0 * st; epi = 20.0; break;   // (C1, S) pairs: two lanes per evaluation
         }
         const double cost = base / (util * fill * ((double)d / (d + epi)));
         if (cost < best - 1e-9) {
