@@ -5,11 +5,12 @@
 //   k_curve_reset, k_curve_minmax, k_curve_prep, k_curve_reduce
 //                      per-point derived arrays, chi2_0, input checks
 //   for every wave (chunk) of periods:
-//     k_fold_sort      fold on the exact phase lattice (Eq. phase), bucket
-//                      sort by (phase, index), gather the folded curve, pad it
-//                      with its first D_m points (Sect. 2.3.2) and build the
-//                      exact prefix sums that give every moving average
-//                      (Eq. cumsum)
+//     k_fold_sort      fold on the exact phase lattice (Eq. phase), two-level
+//                      bucket sort by (phase, index) (super-buckets in global
+//                      memory, fine buckets in shared memory), gather the
+//                      folded curve, pad it with its first D_m points
+//                      (Sect. 2.3.2) and build the exact prefix sums that give
+//                      every moving average (Eq. cumsum)
 //     k_window_tiles   every duration and T0 start (Eq. N_skip): depth
 //                      (Eqs. k, depth), chi2 - chi2_0 (Eqs. out, in),
 //                      per-period minimum; staged tiles, window_tiles.cuh
