@@ -471,14 +471,14 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
 
     long long* warp_sums = reinterpret_cast<long long*>(smem);
     long long* total = warp_sums + 32;
-    unsigned long long* stage = reinterpret_cast<unsigned long long*>(total + 1);   // keys as read; later rfx
-    unsigned long long* sorted = stage + kFoldSegKeys;                            // keys in fine-bucket order
+    long long* srfx = reinterpret_cast<long long*>(total + 1);                  // rfx in final order (swizzled)
+    unsigned long long* sorted = reinterpret_cast<unsigned long long*>(srfx + kFoldSegKeys);   // keys in fine-bucket order
     uint32_t* fcnt = reinterpret_cast<uint32_t*>(sorted + kFoldSegKeys);
     uint32_t* fcur = fcnt + (1 << kFoldFineLog2);
     uint32_t* sb_cnt = fcur + (1 << kFoldFineLog2);
     uint32_t* sb_start = sb_cnt + (1 << kFoldMaxSbLog2);
-    uint16_t* stage_f = reinterpret_cast<uint16_t*>(sb_start + (1 << kFoldMaxSbLog2));   // fine bucket of stage[q]
-    uint16_t* sorted_f = stage_f + kFoldSegKeys;                                          // of sorted[q]
+    uint16_t* inv = reinterpret_cast<uint16_t*>(sb_start + (1 << kFoldMaxSbLog2));       // final position -> sorted position
+    uint16_t* sorted_f = inv + kFoldSegKeys;                                              // fine bucket of sorted[q]
     int* overflow = reinterpret_cast<int*>(sorted_f + kFoldSegKeys);
 
     for (int q = threadIdx.x; q < nsb; q += blockDim.x) sb_cnt[q] = 0;
@@ -532,8 +532,6 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     static_assert(kFoldSegKeys % kFoldThreads == 0, "staged keys split evenly over the threads");
     static_assert(kPerThread == kScanPer, "one scan pass per super-bucket");
     static_assert(kPerThread % kRankBatch == 0, "gathers issued in whole batches");
-    uint16_t* const inv = stage_f;                                     // reused after the scatter
-    long long* const srfx = reinterpret_cast<long long*>(stage);       // reused after the scatter
     // srfx is read in blocks of kScanPer consecutive entries per thread; the
     // swizzle spreads the 16 lanes of a half-warp over 16 bank pairs
     auto swz = [](uint32_t i) { return i ^ ((i >> 4) & 7u); };
@@ -545,22 +543,22 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
         const unsigned long long* region = keys + (int64_t)sb * kFoldSegKeys;
         for (int f = threadIdx.x; f < (1 << kFoldFineLog2); f += blockDim.x) fcnt[f] = 0;
         __syncthreads();
-        {
-            unsigned long long kv[kPerThread];
+        // a thread's keys of the super-bucket and their fine buckets stay in
+        // registers from the count to the scatter
+        unsigned long long kv[kPerThread];
+        uint32_t kf[kPerThread / 2];   // two 16-bit fine buckets per register
 #pragma unroll
-            for (int u = 0; u < kPerThread; ++u) {
-                const uint32_t q = threadIdx.x + u * kFoldThreads;
-                kv[u] = q < len ? region[q] : 0ull;
-            }
+        for (int u = 0; u < kPerThread; ++u) {
+            const uint32_t q = threadIdx.x + u * kFoldThreads;
+            kv[u] = q < len ? region[q] : 0ull;
+        }
 #pragma unroll
-            for (int u = 0; u < kPerThread; ++u) {
-                const uint32_t q = threadIdx.x + u * kFoldThreads;
-                if (q >= len) break;
-                const uint32_t f = fold_fine((long long)(kv[u] >> ib), sh, mul, fshift) & kFineMask;
-                stage[q] = kv[u];
-                stage_f[q] = (uint16_t)f;
-                atomicAdd(&fcnt[f], 1u);
-            }
+        for (int u = 0; u < kPerThread; ++u) {
+            const uint32_t q = threadIdx.x + u * kFoldThreads;
+            const uint32_t f = fold_fine((long long)(kv[u] >> ib), sh, mul, fshift) & kFineMask;
+            if (u & 1) kf[u >> 1] |= f << 16;
+            else kf[u >> 1] = f;
+            if (q < len) atomicAdd(&fcnt[f], 1u);
         }
         __syncthreads();
         {
@@ -578,11 +576,14 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             }
         }
         __syncthreads();
-        for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
-            const uint32_t f = stage_f[q];
+#pragma unroll
+        for (int u = 0; u < kPerThread; ++u) {
+            const uint32_t q = threadIdx.x + u * kFoldThreads;
+            if (q >= len) break;
+            const uint32_t f = (kf[u >> 1] >> ((u & 1) * 16)) & 0xffffu;
             const uint32_t d = atomicAdd(&fcur[f], 1u);   // fcur[f] ends as the end of bucket f
             if (in_range32(dc.check, 5, d, len)) {
-                sorted[d] = stage[q];
+                sorted[d] = kv[u];
                 sorted_f[d] = (uint16_t)f;
             }
         }
@@ -1589,9 +1590,9 @@ int fold_smem_bytes(int bucket_log2)
     // global path: histogram and starts, scan scratch, staged keys and folded rfx
     const int global_path = (2 << bucket_log2) * (int)sizeof(uint32_t) + 33 * (int)sizeof(long long) +
                             kFoldSegKeys * (int)(sizeof(unsigned long long) + sizeof(long long));
-    // staged path: scan scratch, staged and sorted keys, fine-bucket counts
-    // and ends, super-bucket counts and starts, fine buckets of the staged
-    // and sorted keys, overflow flag
+    // staged path: scan scratch, rfx in final order, keys in fine-bucket
+    // order, fine-bucket counts and ends, super-bucket counts and starts,
+    // inverse permutation, fine buckets of the sorted keys, overflow flag
     const int staged = 33 * (int)sizeof(long long) + 2 * kFoldSegKeys * (int)sizeof(unsigned long long) +
                        (2 << kFoldFineLog2) * (int)sizeof(uint32_t) +
                        2 * (1 << kFoldMaxSbLog2) * (int)sizeof(uint32_t) +
