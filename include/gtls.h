@@ -294,6 +294,11 @@ gtls_status gtls_plan_get_profile(const gtls_plan* plan, gtls_profile* out);
  *   best_idx, best_sde    host, nullable: first index of the largest SDE
  *   median_window         0 => 2 floor(N_P/200) + 1, else odd
  * The computation is the one gtls_search applies to its own chi2(P).
+ * Errors: GTLS_ERR_INVALID_ARG when a pointer is not device memory of the
+ * current device (checked with cudaPointerGetAttributes, which allocates
+ * nothing) or when some chi2 value is not finite and >= 0 (checked on the
+ * device; the outputs are then unspecified); GTLS_ERR_INTERNAL when no SDE
+ * value can be ranked.
  * The first call on a device looks up the array's device address (with
  * cudaGetSymbolAddress) and sets a kernel attribute; make that first call
  * before any stream capture.  All calls share the array and it keeps the

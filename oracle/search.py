@@ -125,14 +125,26 @@ def chi2_zero(y, dy):
 
 
 def search_periods(p: OraclePlan, t, y, dy, sel=None, n_threads=0) -> PeriodResults:
-    lib = _load()
     t = np.ascontiguousarray(t, np.float64)
-    y = np.ascontiguousarray(y, np.float64)
-    dy = np.ascontiguousarray(dy, np.float64)
-    n = t.size
-    if n != p.n:
+    if t.size != p.n:
         raise ValueError("plan was made for a different number of points")
     d_lat, p_int, t_ref = grid.phase_lattice(t, p.periods, p.e)
+    return search_periods_lattice(p, d_lat, p_int, t_ref, y, dy, sel, n_threads)
+
+
+def search_periods_lattice(p: OraclePlan, d_lat, p_int, t_ref, y, dy, sel=None,
+                           n_threads=0) -> PeriodResults:
+    """search_periods with the phase lattice given: point i of period k has
+    phase rho_i = d_lat[i] mod p_int[k] (Eq. phase on the lattice); T0 is
+    t_ref + rho_c 2^-e.  Lets a test fold on a lattice of its own."""
+    lib = _load()
+    y = np.ascontiguousarray(y, np.float64)
+    dy = np.ascontiguousarray(dy, np.float64)
+    d_lat = np.ascontiguousarray(d_lat, np.int64)
+    p_int = np.ascontiguousarray(p_int, np.int64)
+    n = y.size
+    if n != p.n or d_lat.size != n or p_int.size != p.periods.size:
+        raise ValueError("lattice, data and plan sizes differ")
     if sel is None:
         sel = np.arange(p.periods.size, dtype=np.int64)
     sel = np.ascontiguousarray(sel, np.int64)

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -3073,15 +3074,22 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocHead + 2 * kNo
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[64] = {};   // device address of g_noalloc_scratch per device
 
-__global__ void __launch_bounds__(1024) k_argmax_noalloc(int np, const double* __restrict__ sde, double* head)
+// Argmax of SDE (ties: lower index) and a check of the caller's chi2(P): every
+// value must be finite and >= 0 (check 18); an argmax that finds no index
+// (every SDE NaN) records check 17.
+__global__ void __launch_bounds__(1024) k_argmax_noalloc(int np, const double* __restrict__ chi2,
+                                                         const double* __restrict__ sde, double* head)
 {
     __shared__ double bv[1024];
     __shared__ int bi[1024];
+    unsigned int* check = reinterpret_cast<unsigned int*>(head + 4);
     double v = -INFINITY;
-    int idx = 0;
+    int idx = 0x7fffffff;
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const double c = chi2[i];
+        if (!(c >= 0.0 && c <= DBL_MAX)) record_check(check, 18, i, np);
         const double x = sde[i];
-        if (x > v) {
+        if (x > v || (x == v && i < idx)) {
             v = x;
             idx = i;
         }
@@ -3101,9 +3109,30 @@ __global__ void __launch_bounds__(1024) k_argmax_noalloc(int np, const double* _
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        if (bi[0] < 0 || bi[0] >= np) record_check(check, 17, bi[0], np);
         head[8] = bv[0];
         head[9] = __longlong_as_double((long long)bi[0]);
     }
+}
+
+// Where `p` lives: device memory of the current device (or managed memory)
+// is accepted, anything else rejected.  cudaPointerGetAttributes allocates
+// nothing.
+gtls_status noalloc_pointer(const void* p, int dev, const char* what)
+{
+    if (!p) return GTLS_OK;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GTLS_ERR_INVALID_ARG, std::string(what) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(GTLS_ERR_INVALID_ARG, std::string(what) + " must be device memory");
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return fail(GTLS_ERR_INVALID_ARG, std::string(what) + " lives on device " + std::to_string(a.device) +
+                                              ", not on the current device " + std::to_string(dev));
+    return GTLS_OK;
 }
 
 // Device address of the scratch array on the current device; the first call
@@ -3143,6 +3172,10 @@ extern "C" gtls_status gtls_sr_sde_noalloc(const double* chi2, int64_t n_periods
     if (outs < 32) return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
     int dev = -1;
     GTLS_CUDA(cudaGetDevice(&dev));
+    GTLS_TRY(noalloc_pointer(chi2, dev, "chi2"));
+    GTLS_TRY(noalloc_pointer(sde_out, dev, "sde_out"));
+    GTLS_TRY(noalloc_pointer(sr_out, dev, "sr_out"));
+    GTLS_TRY(noalloc_pointer(sde_raw_out, dev, "sde_raw_out"));
     double* head = nullptr;
     GTLS_TRY(noalloc_scratch(dev, &head));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -3161,13 +3194,15 @@ extern "C" gtls_status gtls_sr_sde_noalloc(const double* chi2, int64_t n_periods
     k_median_sde<<<(np + outs - 1) / outs, kMedianThreads, kMedianCap * (int)(sizeof(double) + sizeof(int)), st>>>(
         np, hwin, outs, dq);
     GTLS_CUDA(cudaGetLastError());
-    k_argmax_noalloc<<<1, 1024, 0, st>>>(np, sde_out, head);
+    k_argmax_noalloc<<<1, 1024, 0, st>>>(np, chi2, sde_out, head);
     GTLS_CUDA(cudaGetLastError());
     double res[2] = {0.0, 0.0};
     unsigned int chk[4] = {0, 0, 0, 0};
     GTLS_CUDA(cudaMemcpyAsync(res, head + 8, sizeof res, cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaMemcpyAsync(chk, head + 4, sizeof chk, cudaMemcpyDeviceToHost, st));
     GTLS_CUDA(cudaStreamSynchronize(st));
+    if (chk[0] == 18)
+        return fail(GTLS_ERR_INVALID_ARG, "chi2[" + std::to_string(chk[1]) + "] is not finite and >= 0");
     if (chk[0] != 0)
         return fail(GTLS_ERR_INTERNAL, "device index check " + std::to_string(chk[0]) + " failed");
     long long bidx = 0;

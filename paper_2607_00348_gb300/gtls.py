@@ -401,13 +401,24 @@ def sr_sde_noalloc(chi2, sde, sr=None, sde_raw=None, median_window=0, stream=Non
     allocation by the call); `sde` (and `sr`, `sde_raw` when given) receive
     the spectra.
     """
+    import torch
     lib = load()
+    n = int(chi2.numel())
+    for name, x in (("chi2", chi2), ("sde", sde), ("sr", sr), ("sde_raw", sde_raw)):
+        if x is None:
+            continue
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or not x.is_cuda:
+            raise TypeError(f"{name} must be a float64 CUDA tensor")
+        if not x.is_contiguous() or x.numel() != n:
+            raise ValueError(f"{name} must be contiguous with {n} elements")
+        if x.device != chi2.device:
+            raise ValueError(f"{name} is on {x.device}, chi2 on {chi2.device}")
     bi = ctypes.c_int64(0)
     bs = ctypes.c_double(0.0)
-    n = int(chi2.numel())
-    _check(lib.gtls_sr_sde_noalloc(_ptr(chi2), n, int(median_window), _stream_handle(stream),
-                                   _ptr(sr), _ptr(sde_raw), _ptr(sde), ctypes.byref(bi),
-                                   ctypes.byref(bs)))
+    with torch.cuda.device(chi2.device):
+        _check(lib.gtls_sr_sde_noalloc(_ptr(chi2), n, int(median_window), _stream_handle(stream),
+                                       _ptr(sr), _ptr(sde_raw), _ptr(sde), ctypes.byref(bi),
+                                       ctypes.byref(bs)))
     return int(bi.value), float(bs.value)
 
 

@@ -1,13 +1,20 @@
 """Proposal-network kernels (BF16 tensor-core GEMMs, FP32 accumulation)
 against the FP64 reference in oracle/cnn.py.
 
-The reference runs on the same BF16-rounded parameters and stores its input
-and pooled activations in BF16 too (the `store` hook), so that the pooling
-decisions and the stored values are taken in the kernels' precision; what
-remains is FP32 vs FP64 accumulation and the BF16 rounding of the
-gradients inside the backward GEMMs.  Tolerances: logits within 1e-2 of the
-largest |logit|; every parameter tensor's gradient within 3e-2 relative
-(L2 norm); binning within 1e-6 relative.
+Two references:
+  * the precision model of the kernels: the same BF16-rounded parameters,
+    and the input and pooled activations stored in BF16 (the `store` hook),
+    so that the pooling decisions and stored values are taken in the kernels'
+    precision; what remains is FP32 vs FP64 accumulation and the BF16
+    rounding of the upstream gradients inside the backward GEMMs.  Every
+    gradient element must lie within 2.5e-2 of its tensor's largest |value|
+    plus 5e-2 of its own value (measured: at most 1.5e-2 of the largest);
+    logits within 1e-2 of the largest |logit|;
+  * the plain FP64 network (no store hook, FP32 parameters as given): BF16
+    storage then moves every tensor's gradient by up to about 8 % (L2) and
+    some pooling decisions flip; the bound asserted is 0.12 (L2, per tensor)
+    and 0.1 of the largest |value| element-wise, and the loss within 1e-3.
+Binning within 1e-6 relative.
 """
 
 import numpy as np
@@ -80,9 +87,31 @@ def test_gradients_match_reference():
     assert loss == pytest.approx(loss_ref, rel=1e-3)
     got = cnn.unflatten(g.astype(np.float64))
     for name, _ in cnn.param_shapes():
-        err = np.linalg.norm(got[name] - g_ref[name]) / max(np.linalg.norm(g_ref[name]), 1e-30)
-        assert err < 3e-2, (name, err)
+        ref = g_ref[name]
+        np.testing.assert_allclose(got[name], ref, rtol=5e-2, atol=2.5e-2 * np.abs(ref).max(),
+                                   err_msg=name)
     net.close()
+
+
+@pytest.mark.parametrize("seed,batch", [(1, 6), (4, 8)])
+def test_gradients_against_plain_fp64(seed, batch):
+    # the plain FP64 network: parameters as given, no BF16 storage anywhere
+    import paper_2607_00348_gb300 as pkg
+    flat, x, tgt, mask, _ = _setup(seed, batch)
+    net = pkg.Cnn(8, flat)
+    g, loss = net.gradient(_dev(x), _dev(tgt), _dev(mask), batch)
+    net.close()
+    p64 = cnn.unflatten(flat.astype(np.float64))
+    z_ref, cache = cnn.forward(p64, x)
+    loss_ref, dz = cnn.loss_and_dz(z_ref, tgt, mask)
+    g_ref = cnn.backward(p64, cache, dz)
+    assert loss == pytest.approx(loss_ref, rel=1e-3)
+    got = cnn.unflatten(g.astype(np.float64))
+    for name, _ in cnn.param_shapes():
+        ref = g_ref[name]
+        l2 = np.linalg.norm(got[name] - ref) / np.linalg.norm(ref)
+        peak = np.abs(got[name] - ref).max() / np.abs(ref).max()
+        assert l2 < 0.12 and peak < 0.1, (name, l2, peak)
 
 
 def test_adam_step_applies_the_gradient():

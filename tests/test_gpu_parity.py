@@ -2,10 +2,18 @@
 
 Tolerances (stated for the FP32 window sums of the kernels):
   * grid arrays, duration ranges, best period / duration / T0 indices: exact;
-  * chi2(P): 1e-5 relative; SDE: 1e-3 absolute;
+  * chi2(P): 1e-5 relative (the contract) and 1e-6 of chi2 + |chi2_0 - chi2|
+    (the error budget of the FP32 window sums: C1 = sum r s_k carries at most
+    a few thousand FP32 roundings of delta-chi2 = chi2 - chi2_0, and chi2 is
+    assembled in FP64; measured errors stay near 1e-8 of chi2 on the long
+    curves, so a precision regression of a hundredfold fails here); SDE:
+    1e-3 absolute;
   * per-period argmin (duration, T0 start): exact, or -- where FP32 rounding
-    picks a different window of a near tie -- the oracle's chi2 of the GPU's
-    window lies within 1e-5 relative of the oracle's minimum.
+    picks a different window of a true near tie -- the oracle's chi2 of the
+    GPU's window lies within 1e-7 relative of the oracle's minimum (a few
+    times the measured error, so only windows that FP32 rounding can swap
+    qualify); the exact matches must make up 99 % of a full grid and 95 % of
+    a sample of periods.
 """
 
 import numpy as np
@@ -20,11 +28,27 @@ from . import gpu_helpers as gh
 pytestmark = pytest.mark.gpu
 
 CHI2_RTOL = 1e-5
+CHI2_BUDGET = 1e-6
+NEAR_TIE_RTOL = 1e-7
 SDE_ATOL = 1e-3
 
 
-def _check_argmins(op, t, y, dy, r_or, out, periods_idx=None):
-    """Exact argmin or a valid near-tie alternative; returns #exact."""
+def _check_chi2(got, want, chi2_0):
+    """chi2(P) within the contract and within the FP32 error budget.
+
+    The FP32 part of chi2 is delta-chi2 = chi2 - chi2_0, so its rounding
+    scales with chi2 + |chi2_0 - chi2|: on long curves that is chi2 itself
+    (the fit changes chi2 by about 1 %), on a 5-point curve whose best window
+    removes most of chi2 it is several times chi2."""
+    np.testing.assert_allclose(got, want, rtol=CHI2_RTOL, atol=0)
+    scale = np.abs(want) + np.abs(chi2_0 - want)
+    rel = np.abs(got - want) / scale
+    assert float(rel.max()) < CHI2_BUDGET, float(rel.max())
+    return float(rel.max())
+
+
+def _check_argmins(op, t, y, dy, r_or, out, periods_idx=None, min_exact=0.95):
+    """Exact argmin or a true near-tie alternative; returns #exact."""
     sel = r_or.sel if periods_idx is None else periods_idx
     exact = 0
     for k, p in enumerate(sel):
@@ -36,7 +60,8 @@ def _check_argmins(op, t, y, dy, r_or, out, periods_idx=None):
         st = grid.t0_stride(int(op.dur_pts[jg]), op.dt0)
         assert sg % st == 0
         alt = c[sg // st]
-        assert alt == pytest.approx(r_or.chi2[k], rel=CHI2_RTOL), (p, jg, sg)
+        assert alt == pytest.approx(r_or.chi2[k], rel=NEAR_TIE_RTOL), (p, jg, sg)
+    assert exact >= int(min_exact * len(sel)), (exact, len(sel))
     return exact
 
 
@@ -65,9 +90,8 @@ def test_short_white_full_grid_parity():
     r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, lc.t, lc.y, lc.dy)
     pl = gh.plan_for(lc, lc.baseline_days, cfg)
     res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
-    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
-    exact = _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out)
-    assert exact >= 0.99 * r_or.sel.size
+    _check_chi2(out["chi2"], r_or.chi2, r_or.chi2_0)
+    _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out, min_exact=0.99)
     np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
     np.testing.assert_allclose(out["sr"], sr_or, rtol=CHI2_RTOL, atol=0)
     assert res.period_idx == best_or["period_idx"]
@@ -95,7 +119,7 @@ def test_variants_match_oracle(cfg):
     r_or, sr_or, raw_or, sde_or, best_or = osr.full_search(op, lc.t, lc.y, lc.dy)
     pl = gh.plan_for(lc, lc.baseline_days, c)
     res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
-    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out)
     np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
     assert res.period_idx == best_or["period_idx"]
@@ -117,7 +141,7 @@ def test_per_point_weights_and_ragged_sizes(n, seed):
     pl = gh.plan_for(n, base, cfg)
     res, out = gh.gpu_search(pl, t, y, dy)
     assert res.uniform_dy == 0
-    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, t, y, dy, r_or, out)
     np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
     assert res.period_idx == best_or["period_idx"]
@@ -226,7 +250,7 @@ def test_kepler_like_full_size_sampled_parity():
     sel = np.unique(np.concatenate([np.arange(0, npd, 4000), np.arange(near - 8, near + 9),
                                     [npd - 1]]))
     r_or = osr.search_periods(op, lc.t, lc.y, lc.dy, sel)
-    np.testing.assert_allclose(out["chi2"][sel], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"][sel], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out, sel)
     # the search finds the injected 37-d transit
     assert abs(res.period - 37.0) / 37.0 < 2e-3
@@ -250,7 +274,7 @@ def test_refinement_stage_matches_oracle():
     res, out = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
     assert res.refined == 200
     assert np.array_equal(out["refined"].astype(bool), r_or.refined)
-    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out)
     np.testing.assert_allclose(out["sde"], sde_or, rtol=0, atol=SDE_ATOL)
     assert res.period_idx == best_or["period_idx"]
@@ -270,7 +294,7 @@ def test_long_baseline_full_size_sampled_parity():
     sel = np.unique(np.concatenate([np.arange(0, npd, 20000), np.arange(near - 4, near + 5),
                                     [npd - 1]]))
     r_or = osr.search_periods(op, lc.t, lc.y, lc.dy, sel)
-    np.testing.assert_allclose(out["chi2"][sel], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"][sel], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, lc.t, lc.y, lc.dy, r_or, out, sel)
     assert abs(res.period - 123.4) / 123.4 < 2e-3
     assert res.sde > 9.0
@@ -295,7 +319,7 @@ def test_kepler_like_per_point_weights_sampled_parity():
     sel = np.unique(np.concatenate([np.arange(0, npd, 10000), np.arange(near - 3, near + 4),
                                     [npd - 1]]))
     r_or = osr.search_periods(op, lc.t, lc.y, dy, sel)
-    np.testing.assert_allclose(out["chi2"][sel], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"][sel], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, lc.t, lc.y, dy, r_or, out, sel)
     assert abs(res.period - 37.0) / 37.0 < 2e-3
     pl.close()
@@ -320,7 +344,7 @@ def test_phase_pile_up_takes_the_global_memory_fold():
     r_or = osr.search_periods(op, t, y, dy)
     pl = gh.plan_for(n, base, periods_days=periods)
     res, out = gh.gpu_search(pl, t, y, dy)
-    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, t, y, dy, r_or, out)
     pl.close()
 
@@ -353,6 +377,6 @@ def test_durations_longer_than_a_tile_take_the_window_kernel():
     r_or = osr.search_periods(op, t, y, dy)
     pl = gh.plan_for(n, base, periods_days=periods)
     res, out = gh.gpu_search(pl, t, y, dy)
-    np.testing.assert_allclose(out["chi2"], r_or.chi2, rtol=CHI2_RTOL, atol=0)
+    _check_chi2(out["chi2"], r_or.chi2, r_or.chi2_0)
     _check_argmins(op, t, y, dy, r_or, out)
     pl.close()

@@ -59,3 +59,33 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     big = torch.ones((1 << 19) + 1, dtype=torch.float64, device=dev)
     with pytest.raises(binding.GtlsError, match="INVALID_ARG"):
         binding.sr_sde_noalloc(big, torch.empty_like(big))
+
+
+def test_noalloc_rejects_bad_spectra_and_buffers():
+    import torch
+
+    from paper_2607_00348_gb300 import gtls as binding
+
+    dev = torch.device("cuda:0")
+    chi2 = torch.linspace(100.0, 200.0, 3000, dtype=torch.float64, device=dev)
+    sde = torch.empty_like(chi2)
+    for bad in (float("nan"), float("inf"), -1.0):
+        c = chi2.clone()
+        c[1234] = bad
+        with pytest.raises(binding.GtlsError, match="INVALID_ARG.*chi2"):
+            binding.sr_sde_noalloc(c, sde)
+    with pytest.raises(TypeError):
+        binding.sr_sde_noalloc(chi2, torch.empty(3000, dtype=torch.float32, device=dev))
+    with pytest.raises(ValueError):
+        binding.sr_sde_noalloc(chi2, torch.empty(2999, dtype=torch.float64, device=dev))
+    with pytest.raises(TypeError):
+        binding.sr_sde_noalloc(chi2, torch.empty(3000, dtype=torch.float64))
+    # host memory handed straight to the C entry point is refused there
+    lib = binding.load()
+    host = np.zeros(3000)
+    st = lib.gtls_sr_sde_noalloc(binding._ptr(chi2), 3000, 0, binding._stream_handle(None),
+                                 None, None, host.ctypes.data, None, None)
+    assert st == 1 and b"device memory" in lib.gtls_last_error()
+    # a good call afterwards still works
+    bi, bs = binding.sr_sde_noalloc(chi2, sde)
+    assert 0 <= bi < 3000 and np.isfinite(bs)
