@@ -76,7 +76,11 @@ typedef struct {
     int32_t refine_periods;     /* K > 0: re-search the K best periods by SDE(P) with T0 step 1
                                    (Sect. 2.5, two-stage T0 search), then recompute SR/SDE;
                                    0 => coarse pass only (default) */
-    int32_t reserved1;
+    int32_t test_flags;         /* 0 for searches (default).  Bit 0: before its first work item
+                                   the tensor-core window kernel waits about 1 ms on a barrier
+                                   phase that nothing completes, records the timeout and stops,
+                                   so that the search returns GTLS_ERR_TIMEOUT: a test of the
+                                   bounded-wait path that faults nothing */
 } gtls_plan_params;
 
 /* Sizes of a plan (host struct filled by gtls_plan_get_info). */

@@ -48,6 +48,8 @@ struct DevPlan {
     const int32_t* cfg_nc_w;    // per-point weights: lanes per window block per duration
     int32_t median_half;        // half width h of the running-median window
     int32_t refine_k;           // periods re-searched with T0 step 1 (0: none)
+    const int64_t* tc_off;      // offset of duration j in tc_tab (floats; kTensor durations)
+    const float* tc_tab;        // tensor-core template chunks: [chunk][hi, lo][32 x 32 core-matrix layout]
 };
 
 // What the fold gathers for one point, in one 16-byte load.
@@ -162,6 +164,14 @@ struct gtls_plan {
     // durations too long for a tile (marked kWindowOnly): searched by the
     // one-thread-per-window kernel in the same waves
     bool has_window_only = false, has_window_only_ref = false;
+    // durations on the tensor-core window kernel (kTensor), the widest
+    // [jlo, jhi] span of a period (work items per period of that kernel),
+    // its counter, and the timeout test (a wait that nothing completes)
+    bool has_tensor = false;
+    int tc_jspan = 0;
+    unsigned int* tc_counter = nullptr;
+    int tc_test_wait = 0;
+    const void* tc_maps = nullptr;      // TMA maps of dk.rs (made with the chunk scratch)
     std::vector<int32_t> variant_host;   // window-kernel variant per duration (host copy)
     int n_sm = 0;
     unsigned int* tile_counter = nullptr;

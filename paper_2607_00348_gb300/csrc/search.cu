@@ -21,6 +21,8 @@
 //   k_topk + waves with T0 step 1           refinement of the best periods
 //                                           (Sect. 2.5), then SR/SDE again
 //   k_best                                  the candidate of largest SDE
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,7 +78,11 @@ constexpr int kSearchThreads = 256;
 constexpr int kMedianThreads = 1024;
 constexpr int kMedianCap = 8192;       // values a median block sorts in shared memory
 constexpr double kRScale = 1099511627776.0;   // 2^40: fixed point of r = 1 - y
-constexpr int64_t kPadMargin = 64;
+// zeros after the padded folded curve: the tensor-core window kernel reads
+// whole rows of up to tc::kMaxSigma points (two rows and a T0 step past the
+// last window's end; their template entries are zero, their values must be
+// finite)
+constexpr int64_t kPadMargin = 3 * 1024 + 64;
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -227,6 +233,7 @@ __host__ __device__ __forceinline__ int prep_blocks_for(int64_t n)
 }  // namespace
 
 #include "window_tiles.cuh"
+#include "window_tc.cuh"
 
 namespace {
 
@@ -1051,7 +1058,9 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
                         }
                     }
                     const int nwin = max(0, t.m_b - t.m_a);
-                    t.tasks = (!weighted && t.variant == kWindowOnly) ? 0 : (nwin + t.per_task - 1) / t.per_task;
+                    t.tasks = (!weighted && (t.variant == kWindowOnly || t.variant == kTensor))
+                                  ? 0
+                                  : (nwin + t.per_task - 1) / t.per_task;
                     t.jrows = jrows;
                     t.tg = dp.tmpl + dp.tmpl_off[j];
                     t.tg2 = weighted ? dp.tmplw + dp.tmplw_off[j] : dp.tmpl2 + dp.tmpl2_off[j];
@@ -1149,6 +1158,436 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int b
             atomicMin(&ds.outs[lc].best[p], b);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core window search (uniform weights): see window_tc.cuh
+// ---------------------------------------------------------------------------
+
+// Row pitch (points) of duration j on the tensor-core kernel: g = 4 / gcd(st, 4)
+// windows per row, so that rows start on 16-byte boundaries.
+__host__ __device__ __forceinline__ int tc_windows_per_row(int st) { return (st & 3) == 0 ? 1 : ((st & 1) ? 4 : 2); }
+
+// Row blocks I of a window of d points: ceil((d + (g - 1) st) / sigma).
+__host__ __device__ __forceinline__ int tc_row_blocks(int d, int st, int g)
+{
+    const int sigma = g * st;
+    return (d + (g - 1) * st + sigma - 1) / sigma;
+}
+
+// Producer: items (slot, duration) from the device counter, item = slot *
+// jspan + (j - jlo); per chunk the description, the TMA load of the rows and
+// the bulk copy of B into the next stage of the ring; finally an end marker.
+__device__ void tc_producer(const DevSet& ds, const SlotMap& sm, const DevChunk& dk, const void* maps, int jspan,
+                            unsigned int* counter, tc::TcSmem& S, int test_wait)
+{
+    using namespace tc;
+    volatile int* abort = &S.abort;
+    const uint32_t a_base = smem_addr(&S.a[0][0]), b_base = smem_addr(&S.b[0][0]);
+    const uint32_t full0 = smem_addr(&S.full[0]), af0 = smem_addr(&S.a_free[0]), bf0 = smem_addr(&S.b_free[0]);
+    const int total = sm.slots * jspan;
+    uint32_t c = 0;
+    bool ok = true;
+    if (test_wait) {
+        // timeout test: a wait on a barrier phase that nothing completes (no
+        // MMA can be committed before the first chunk is issued)
+        if (!mbar_wait(smem_addr(&S.t_free[0]), 0u, kTestWaitCycles)) {
+            record_check(ds.curves[0].check, kCheckTimeout, 1, 0);
+            *abort = 1;
+            ok = false;
+        }
+    }
+    // a stage is free once the converters read its rows and the MMAs its B
+    auto claim = [&](uint32_t cc) -> bool {
+        if (cc < kStages) return true;
+        const uint32_t s = cc % kStages, par = ((cc - kStages) / kStages) & 1u;
+        if (mbar_wait(af0 + 8 * s, par, kWaitCycles, abort) && mbar_wait(bf0 + 8 * s, par, kWaitCycles, abort))
+            return true;
+        if (!*abort) record_check(ds.curves[0].check, kCheckTimeout, (long long)cc, 8);
+        *abort = 1;
+        return false;
+    };
+    while (ok) {
+        const int item = (int)atomicAdd(counter, 1u);
+        if (item >= total) break;
+        const int slot = item / jspan, jj = item - slot * jspan;
+        int lc = 0, p = 0;
+        if (!resolve_slot(ds, sm, slot, lc, p)) continue;
+        const DevPlan& dp = ds.plans[lc];
+        const int j = dp.jlo[p] + jj;
+        if (j > dp.jhi[p] || (jj > 0 && dp.dpts[j] == dp.dpts[j - 1]) || dp.cfg_variant[j] != tiles::kTensor)
+            continue;
+        unsigned int* const check = ds.curves[lc].check;
+        const int64_t n = dp.n;
+        const int d = dp.dpts[j], st = dp.stride[j];
+        const int g = tc_windows_per_row(st);
+        const int sigma = g * st;
+        const int nblk = tc_row_blocks(d, st, g);
+        const int ksteps = (sigma + 7) >> 3;
+        const int nch = (ksteps + 3) >> 2;
+        const int64_t nwin = (n + st - 1) / st;
+        const int64_t wrows = (nwin + g - 1) / g;        // rows that start windows
+        const int per_tile = kRows - (nblk - 1);
+        const int64_t tiles_n = (wrows + per_tile - 1) / per_tile;
+        if (!in_range(check, 31, nblk * g, kN + 1) || !in_range(check, 32, sigma / 4 - 1, kMaps) ||
+            !in_range(check, 33, (wrows + nblk - 1) * (int64_t)sigma, n + dp.dmax_p[p] + kPadMargin + 1) ||
+            !in_range(check, 34, d, dp.dmax_p[p] + 1) || !in_range(check, 35, tiles_n, 1ll << 24))
+            continue;
+        const void* map = static_cast<const unsigned char*>(maps) + (size_t)(sigma / 4 - 1) * 128;
+        const float* tab = dp.tc_tab + dp.tc_off[j];
+        ChunkInfo ci{};
+        ci.end = 0;
+        ci.lc = lc;
+        ci.p = p;
+        ci.j = j;
+        ci.st = st;
+        ci.d = d;
+        ci.g = g;
+        ci.nblk = nblk;
+        ci.per_tile = per_tile;
+        ci.nwin = nwin;
+        ci.slot = slot;
+        ci.w_uni = (float)ds.curves[lc].scal[2];
+        ci.inv_sum_t = dp.inv_sum_t[j] * (1.0f / 1099511627776.0f);
+        ci.sum_t2 = dp.sum_t2[j];
+        for (int64_t t = 0; t < tiles_n && ok; ++t) {
+            for (int kc = 0; kc < nch; ++kc) {
+                if (!claim(c)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t s = c % kStages;
+                ci.kc = kc;
+                ci.ksteps = min(4, ksteps - kc * 4);
+                ci.kst_tile = ksteps;
+                ci.first = kc == 0;
+                ci.last = kc == nch - 1;
+                ci.item_last = ci.last && t == tiles_n - 1;
+                ci.tile = (int)t;
+                S.info[s] = ci;
+                mbar_expect_tx(full0 + 8 * s, kBytesA + kBytesB);
+                tma_load_3d(a_base + s * kBytesA, map, kc * kChunk, (int)(t * per_tile), slot, full0 + 8 * s);
+                bulk_load(b_base + s * kBytesB, tab + (size_t)kc * 2 * kN * kChunk, kBytesB, full0 + 8 * s);
+                ++c;
+            }
+        }
+    }
+    bool marked = false;
+    if (ok && claim(c)) {
+        const uint32_t s = c % kStages;
+        S.info[s].end = 1;
+        mbar_arrive(full0 + 8 * s);
+        marked = true;
+    }
+    // copies in flight land before the CTA frees its memory (the stage that
+    // took the end marker has moved on by one phase: its last chunk is done)
+    const uint32_t lo = c >= kStages ? c - kStages + (marked ? 1u : 0u) : 0u;
+    for (uint32_t cc = lo; cc < c; ++cc)
+        mbar_wait(full0 + 8 * (cc % kStages), (cc / kStages) & 1u, kWaitCycles);
+}
+
+// MMA thread w (0..3): k-step w of every chunk, its three tcgen05.mma (A
+// from the chunk's TMEM stage, B from its shared-memory stage) into
+// accumulator w of the tile's D buffer; every chunk is committed to the
+// barriers that free the TMEM stage and B, and a tile's last chunk to the
+// tile's D barrier (each of them counts the four threads).
+__device__ void tc_mma(tc::TcSmem& S, uint32_t tmem, unsigned int* check0, int w)
+{
+    using namespace tc;
+    volatile int* abort = &S.abort;
+    const uint32_t b_base = smem_addr(&S.b[0][0]);
+    const uint32_t full0 = smem_addr(&S.full[0]), bf0 = smem_addr(&S.b_free[0]);
+    const uint32_t tf0 = smem_addr(&S.t_full[0]), tr0 = smem_addr(&S.t_free[0]);
+    const uint32_t df0 = smem_addr(&S.d_full[0]), dr0 = smem_addr(&S.d_free[0]);
+    const uint32_t if0 = smem_addr(&S.i_full[0]);
+    uint32_t tile_seq = 0, committed = 0;
+    bool ok = true;
+    int where = 0;
+    for (uint32_t c = 0;; ++c) {
+        const uint32_t s = c % kStages, ts = c % kTStages;
+        if (!mbar_wait(full0 + 8 * s, (c / kStages) & 1u, kWaitCycles, abort)) {
+            ok = false;
+            where = 5;
+            break;
+        }
+        // a copy: the stage (and its description) is refilled as soon as
+        // the four threads commit it to b_free
+        const ChunkInfo ci = S.info[s];
+        if (ci.end) {
+            if (w == 0) {
+                // end marker for the epilogue, once it left this D buffer
+                const uint32_t db = tile_seq & 1u;
+                if (tile_seq >= 2 && !mbar_wait(dr0 + 8 * db, ((tile_seq - 2) >> 1) & 1u, kWaitCycles, abort)) {
+                    ok = false;
+                    where = 9;
+                    break;
+                }
+                S.tinfo[db].end = 1;
+                mbar_arrive(if0 + 8 * db);
+            }
+            break;
+        }
+        const int kc = ci.kc, ksteps = ci.ksteps, first = ci.first, last = ci.last;
+        if (!mbar_wait(tf0 + 8 * ts, (c / kTStages) & 1u, kWaitCycles, abort)) {
+            ok = false;
+            where = 6;
+            break;
+        }
+        const uint32_t db = tile_seq & 1u;
+        if (first && tile_seq >= 2 && !mbar_wait(dr0 + 8 * db, ((tile_seq - 2) >> 1) & 1u, kWaitCycles, abort)) {
+            ok = false;
+            where = 7;
+            break;
+        }
+        fence_after();
+        if (w < ksteps) {
+            const uint32_t a_col = tmem + ts * 64u + (uint32_t)(w * 8);
+            const uint32_t d_col = tmem + kDCol + db * (kMmaWarps * 32u) + (uint32_t)(w * 32);
+            const uint32_t bh = b_base + s * kBytesB + (uint32_t)(w * 256), bl = bh + kBytesB / 2;
+            const uint64_t dh = smem_desc(bh, 128, 1024);
+            const uint64_t dl = smem_desc(bl, 128, 1024);
+            mma_tf32(d_col, a_col, dh, kc > 0 ? 1u : 0u);
+            mma_tf32(d_col, a_col, dl, 1u);
+            mma_tf32(d_col, a_col + 32, dh, 1u);
+        }
+        mma_commit(tr0 + 8 * ts);
+        mma_commit(bf0 + 8 * s);
+        if (last) {
+            mma_commit(df0 + 8 * db);
+            if (w == 0) {
+                S.tinfo[db] = ci;
+                mbar_arrive(if0 + 8 * db);
+            }
+            ++tile_seq;
+        }
+        committed = c + 1;
+    }
+    if (!ok) {
+        if (!*abort) record_check(check0, kCheckTimeout, (long long)committed, where * 10 + w);
+        *abort = 1;
+    }
+    // the MMAs complete before the CTA frees TMEM
+    if (committed > 0) {
+        const uint32_t c = committed - 1, ts = c % kTStages;
+        mbar_wait(tr0 + 8 * ts, (c / kTStages) & 1u, kWaitCycles);
+    }
+}
+
+// Converter warps (TMEM lanes 0..127): the rows of every chunk to a TMEM
+// stage in TF32 halves.
+__device__ void tc_convert(const DevSet& ds, tc::TcSmem& S, uint32_t tmem)
+{
+    using namespace tc;
+    volatile int* abort = &S.abort;
+    unsigned int* const check0 = ds.curves[0].check;
+    const int l = threadIdx.x;   // 0..127
+    const uint32_t lane_field = (uint32_t)((l >> 5) * 32) << 16;
+    const uint32_t full0 = smem_addr(&S.full[0]), af0 = smem_addr(&S.a_free[0]);
+    const uint32_t tf0 = smem_addr(&S.t_full[0]), tr0 = smem_addr(&S.t_free[0]);
+    bool fail = false;
+    for (uint32_t c = 0;; ++c) {
+        const uint32_t s = c % kStages, ts = c % kTStages;
+        if (!fail && !mbar_wait(full0 + 8 * s, (c / kStages) & 1u, kWaitCycles, abort)) {
+            fail = true;
+            record_check(check0, kCheckTimeout, (long long)c, 1);
+            *abort = 1;
+        }
+        const int end = S.info[s].end;
+        float v[32];
+        {
+            const float4* row = reinterpret_cast<const float4*>(&S.a[s][l * kChunk]);
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4) {
+                const float4 x = row[c4 ^ (l & 7)];
+                v[4 * c4] = x.x;
+                v[4 * c4 + 1] = x.y;
+                v[4 * c4 + 2] = x.z;
+                v[4 * c4 + 3] = x.w;
+            }
+        }
+        // the MMAs of chunk c - kTStages read this TMEM stage
+        if (!fail && c >= kTStages &&
+            !mbar_wait(tr0 + 8 * ts, ((c - kTStages) / kTStages) & 1u, kWaitCycles, abort)) {
+            fail = true;
+            record_check(check0, kCheckTimeout, (long long)c, 2);
+            *abort = 1;
+        }
+        const uint32_t a_col = tmem + ts * 64u + lane_field;
+        {
+            uint32_t h[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) h[k] = __float_as_uint(v[k]) & 0xffffe000u;
+            tmem_st32(a_col, h);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) h[k] = __float_as_uint(v[k] - __uint_as_float(h[k]));
+            tmem_st32(a_col + 32, h);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        if (bar_sync_or(1, 128, fail)) break;
+        if (end) break;    // every lane read the same marker
+        if (l == 0) {
+            mbar_arrive(af0 + 8 * s);
+            mbar_arrive(tf0 + 8 * ts);
+        }
+    }
+}
+
+// Epilogue warps: every tile once its MMAs completed.  Lane l of warp w owns
+// row 32 (w % 4) + l (the TMEM lanes its warp may read).
+__device__ void tc_epilogue(const DevSet& ds, const SlotMap& sm, const DevChunk& dk, tc::TcSmem& S, uint32_t tmem,
+                            int quad)
+{
+    using namespace tc;
+    volatile int* abort = &S.abort;
+    unsigned int* const check0 = ds.curves[0].check;
+    const int l = quad * 32 + (threadIdx.x & 31);
+    const uint32_t lane_field = (uint32_t)(quad * 32) << 16;
+    const uint32_t df0 = smem_addr(&S.d_full[0]), dr0 = smem_addr(&S.d_free[0]);
+    const uint32_t if0 = smem_addr(&S.i_full[0]);
+    bool fail = false;
+    unsigned long long best = ~0ull;
+    for (uint32_t tile_seq = 0;; ++tile_seq) {
+        const uint32_t db = tile_seq & 1u, par = (tile_seq >> 1) & 1u;
+        if (!fail && !mbar_wait(if0 + 8 * db, par, kWaitCycles, abort)) {
+            fail = true;
+            record_check(check0, kCheckTimeout, (long long)tile_seq, 3);
+            *abort = 1;
+        }
+        const ChunkInfo pi = S.tinfo[db];
+        // the description must name a slot of this wave and the curve and
+        // period that slot holds (checked before any memory access it steers)
+        bool valid = false;
+        if (!fail && !pi.end) {
+            int lc2 = -1, p2 = -1;
+            valid = pi.slot >= 0 && pi.slot < sm.slots && resolve_slot(ds, sm, (int)pi.slot, lc2, p2) &&
+                    lc2 == pi.lc && p2 == pi.p;
+            if (!valid && l == 0) record_check(check0, 36, pi.slot, pi.p);
+        }
+        // prefix sums of the windows of this lane's row
+        long long pa[4] = {0, 0, 0, 0}, pb[4] = {0, 0, 0, 0};
+        if (valid) {
+            const long long* pf = dk.pf + pi.slot * dk.pad_stride;
+            const int64_t rho = (int64_t)pi.tile * pi.per_tile + l;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t m = rho * pi.g + q;
+                if (q < pi.g && l < pi.per_tile && m < pi.nwin) {
+                    pa[q] = pf[m * pi.st];
+                    pb[q] = pf[m * pi.st + pi.d];
+                }
+            }
+        }
+        if (!fail && !pi.end && !mbar_wait(df0 + 8 * db, par, kWaitCycles, abort)) {
+            fail = true;
+            record_check(check0, kCheckTimeout, (long long)tile_seq, 4);
+            *abort = 1;
+        }
+        float gsum[32];
+        if (!fail && !pi.end) {
+            fence_after();
+            uint32_t gv[32];
+            const uint32_t dcol = tmem + kDCol + db * (kMmaWarps * 32u) + lane_field;
+            tmem_ld32(dcol, gv);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) gsum[c] = __uint_as_float(gv[c]);
+            const int nacc = min(kMmaWarps, pi.kst_tile);
+            for (int a = 1; a < nacc; ++a) {
+                tmem_ld32(dcol + (uint32_t)(a * 32), gv);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) gsum[c] += __uint_as_float(gv[c]);
+            }
+            fence_before();
+        }
+        // every lane read its accumulators (and the last tile's G was used)
+        if (bar_sync_or(2, 128, fail)) break;
+        if (pi.end) break;
+        if (l == 0) mbar_arrive(dr0 + 8 * db);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) S.g[l * 32 + (c ^ (l & 31))] = gsum[c];
+        bar_sync(2, 128);
+        if (valid && l < pi.per_tile) {
+            const int64_t rho = (int64_t)pi.tile * pi.per_tile + l;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t m = rho * pi.g + q;
+                if (q < pi.g && m < pi.nwin) {
+                    float c1 = 0.0f;
+                    for (int i = 0; i < pi.nblk; ++i) {
+                        const int r = l + i;
+                        c1 += S.g[r * 32 + ((i * pi.g + q) ^ (r & 31))];
+                    }
+                    const float depth = fmaxf(0.0f, tiles::fixed_to_float(pb[q] - pa[q]) * pi.inv_sum_t);
+                    const float dchi = pi.w_uni * depth * fmaf(depth, pi.sum_t2, -2.0f * c1);
+                    const unsigned long long key = ((unsigned long long)float_order_key(dchi) << 32) |
+                                                   ((unsigned long long)pi.j << 24) | (unsigned long long)m;
+                    best = key < best ? key : best;
+                }
+            }
+        }
+        if (pi.item_last) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+                best = w < best ? w : best;
+            }
+            if ((l & 31) == 0 && best != ~0ull && valid) atomicMin(&ds.outs[pi.lc].best[pi.p], best);
+            best = ~0ull;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+k_window_tc(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, const void* maps, int jspan,
+            unsigned int* counter, int test_wait)
+{
+    using namespace tc;
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint32_t s_tmem;
+    TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        S.tinfo[0].end = 0;
+        S.tinfo[1].end = 0;
+        auto init = [](unsigned long long* b, int n, int count) {
+            for (int i = 0; i < n; ++i)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b + i)), "r"(count) : "memory");
+        };
+        init(S.full, kStages, 1);
+        init(S.a_free, kStages, 1);
+        init(S.b_free, kStages, kMmaWarps);
+        init(S.t_full, kTStages, 1);
+        init(S.t_free, kTStages, kMmaWarps);
+        init(S.d_full, 2, kMmaWarps);
+        init(S.d_free, 2, 1);
+        init(S.i_full, 2, 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    if (warp < kConvWarps) {
+        tc_convert(ds, S, tmem);
+    } else if (warp == kConvWarps) {
+        if (lane == 0) tc_producer(ds, sm, dk, maps, jspan, counter, S, test_wait);
+    } else if (warp < kConvWarps + 1 + kMmaWarps) {
+        if (lane == 0) tc_mma(S, tmem, ds.curves[0].check, warp - kConvWarps - 1);
+    } else {
+        tc_epilogue(ds, sm, dk, S, tmem, warp % 4);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1630,6 +2069,8 @@ gtls_status configure_kernels(int dev)
     GTLS_TRY(allow((const void*)k_median_sde));
     GTLS_TRY(allow((const void*)k_median_sde_set));
     GTLS_TRY(allow((const void*)k_topk));
+    GTLS_CUDA(cudaFuncSetAttribute((const void*)k_window_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   tc::kSmemRequest));
     done.push_back(dev);
     return GTLS_OK;
 }
@@ -1656,6 +2097,7 @@ gtls_status create_device(gtls_plan* pl)
     if (median_outs(dp.median_half) < 32)
         return fail(GTLS_ERR_INVALID_ARG, "median window too large for the device median");
     dp.refine_k = std::min<int>(h.prm.refine_periods, dp.np);
+    pl->tc_test_wait = (h.prm.test_flags & 1) ? 1 : 0;
     GTLS_TRY(configure_kernels(pl->device));
     std::vector<float> inv_sum_t(dp.nd), sum_t2f(dp.nd);
     for (int j = 0; j < dp.nd; ++j) {
@@ -1822,6 +2264,66 @@ gtls_status create_device(gtls_plan* pl)
                 }
             }
         }
+        // uniform-weight durations whose T0 step is at least the tensor-core
+        // threshold, whose rows (sigma = g st points, g = 4 / gcd(st, 4)) are
+        // at most tc::kMaxSigma long and whose window spans I g <= 32 template
+        // rows go to the tensor-core kernel; its table holds, per duration and
+        // K chunk of 32 columns, B[i g + q][c] = s_{i sigma + c - q st} (zero
+        // outside the template and past sigma), split into TF32 halves (round
+        // to nearest) in the canonical K-major core-matrix layout: element
+        // (row, c) at float (row / 8) 256 + (c / 4) 32 + (row % 8) 4 + c % 4
+        std::vector<int64_t> tc_off(dp.nd, 0);
+        std::vector<float> tc_tab;
+        {
+            int tc_min = tc::kMinStDefault;
+            if (const char* e = std::getenv("GTLS_TC_MIN_ST")) tc_min = std::max(2, std::atoi(e));
+            pl->has_tensor = false;
+            pl->has_window_only = false;
+            auto tf32_rn = [](float x) {
+                uint32_t b;
+                std::memcpy(&b, &x, 4);
+                b = (b + 0x1000u) & 0xffffe000u;
+                float y;
+                std::memcpy(&y, &b, 4);
+                return y;
+            };
+            for (int j = 0; j < dp.nd && pl->tile_ok; ++j) {
+                const int st = h.stride[j], d = h.dpts[j];
+                const int g = tc_windows_per_row(st), sigma = g * st;
+                const int nblk = sigma <= tc::kMaxSigma ? tc_row_blocks(d, st, g) : tc::kN + 1;
+                if (st >= tc_min && sigma <= tc::kMaxSigma && nblk * g <= tc::kN && d <= h.n) {
+                    var[j] = tiles::kTensor;
+                    ncs[j] = 32;
+                    const int ksteps = (sigma + 7) / 8, nch = (ksteps + 3) / 4;
+                    tc_off[j] = (int64_t)tc_tab.size();
+                    tc_tab.resize(tc_tab.size() + (size_t)nch * 2 * tc::kN * tc::kChunk, 0.0f);
+                    float* tb = tc_tab.data() + tc_off[j];
+                    const float* tj = h.tmpl.data() + h.tmpl_off[j];
+                    for (int kc = 0; kc < nch; ++kc)
+                        for (int i = 0; i < nblk; ++i)
+                            for (int q = 0; q < g; ++q)
+                                for (int c = 0; c < tc::kChunk; ++c) {
+                                    const int row = i * g + q, col = kc * tc::kChunk + c;
+                                    const int64_t k = (int64_t)i * sigma + col - (int64_t)q * st;
+                                    const float v = (col < sigma && k >= 0 && k < d) ? tj[k] : 0.0f;
+                                    const float hi = tf32_rn(v);
+                                    const float lo = tf32_rn(v - hi);
+                                    const size_t e = (size_t)(row / 8) * 256 + (size_t)(c / 4) * 32 + (row % 8) * 4 +
+                                                     c % 4;
+                                    tb[(size_t)kc * 2 * tc::kN * tc::kChunk + e] = hi;
+                                    tb[(size_t)kc * 2 * tc::kN * tc::kChunk + tc::kN * tc::kChunk + e] = lo;
+                                }
+                    pl->has_tensor = true;
+                }
+                if (var[j] == tiles::kWindowOnly) pl->has_window_only = true;
+            }
+            int span = 1;
+            for (int p = 0; p < dp.np; ++p) span = std::max(span, h.jhi[p] - h.jlo[p] + 1);
+            pl->tc_jspan = span;
+            if (tc_tab.empty()) tc_tab.assign(4, 0.0f);
+        }
+        GTLS_TRY(upload(pl, const_cast<int64_t**>(&dp.tc_off), tc_off));
+        GTLS_TRY(upload(pl, const_cast<float**>(&dp.tc_tab), tc_tab));
         GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_variant), var));
         pl->variant_host = var;
         GTLS_TRY(upload(pl, const_cast<int32_t**>(&dp.cfg_nc), ncs));
@@ -1930,6 +2432,7 @@ gtls_status create_device(gtls_plan* pl)
             GTLS_TRY(upload(pl, const_cast<int32_t**>(&pl->dp_ref.cfg_variant), var1));
         }
         GTLS_TRY(dev_alloc(pl, &pl->tile_counter, 1));
+        GTLS_TRY(dev_alloc(pl, &pl->tc_counter, 1));
     }
 
     // one-entry descriptor sets of this plan's own searches
@@ -1951,6 +2454,44 @@ gtls_status create_device(gtls_plan* pl)
     return GTLS_OK;
 }
 
+// TMA descriptors of the tensor-core window kernel over the folded curves of
+// a chunk scratch: map k reads dk.rs as rows of sigma = 4 (k + 1) points,
+// 3-D (column < sigma, row < pad_stride / sigma, slot < chunk), boxes of 32
+// columns x 128 rows x 1 slot into 128-byte-swizzled shared memory; columns
+// and rows outside read as zeros.  Written to `dev` (tc::kMaps x 128 bytes).
+gtls_status make_tc_maps(const DevChunk& dk, void* dev)
+{
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            GTLS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+            if (!fn || q != cudaDriverEntryPointSuccess)
+                return fail(GTLS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    std::vector<CUtensorMap> maps(tc::kMaps);
+    for (int k = 0; k < tc::kMaps; ++k) {
+        const uint64_t sigma = 4ull * (uint64_t)(k + 1);
+        const cuuint64_t dims[3] = {sigma, (cuuint64_t)dk.pad_stride / sigma, (cuuint64_t)dk.chunk};
+        const cuuint64_t strides[2] = {sigma * 4ull, (cuuint64_t)dk.pad_stride * 4ull};
+        const cuuint32_t box[3] = {(cuuint32_t)tc::kChunk, (cuuint32_t)tc::kRows, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult r = encode(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, dk.rs, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(GTLS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a row pitch of " + std::to_string(sigma) +
+                                           " points (error " + std::to_string((int)r) + ")");
+    }
+    GTLS_CUDA(cudaMemcpy(dev, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return GTLS_OK;
+}
+
 // The chunk scratch of a plan's own searches (batches bring their own).
 gtls_status ensure_chunk(gtls_plan* pl)
 {
@@ -1963,6 +2504,12 @@ gtls_status ensure_chunk(gtls_plan* pl)
     GTLS_TRY(dev_alloc(pl, &dk.ws, chunk * dk.pad_stride));
     GTLS_TRY(dev_alloc(pl, &dk.wrs, chunk * dk.pad_stride));
     GTLS_TRY(dev_alloc(pl, &dk.pf, chunk * dk.pad_stride));
+    if (pl->has_tensor) {
+        unsigned char* maps = nullptr;
+        GTLS_TRY(dev_alloc(pl, &maps, (size_t)tc::kMaps * sizeof(CUtensorMap)));
+        GTLS_TRY(make_tc_maps(dk, maps));
+        pl->tc_maps = maps;
+    }
     pl->chunk_ready = true;
     return GTLS_OK;
 }
@@ -2015,6 +2562,9 @@ struct Ctx {
     int median_blocks = 1;   // widest row of the running-median grid
     int topk_smem = 0;
     cudaStream_t st = nullptr;
+    const void* tc_maps = nullptr;   // tensor-core kernel: TMA maps of dk.rs (tc::kMaps rows pitches)
+    int tc_jspan = 1;        // tensor-core kernel: work items per period slot
+    int tc_test = 0;         // tensor-core kernel: run the timeout test
     int64_t launches = 0, window_launches = 0;
     gtls_plan* prof = nullptr;   // stage marks (single search with profiling on)
     size_t ev = 0;
@@ -2028,7 +2578,8 @@ gtls_status stage_mark(Ctx& c, int stage)
 // One wave: fold + sort, every window, per-period results.  `counter` must
 // be zero when the window kernel starts (reset here when reset_counter).
 gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weighted, bool window_only,
-                      unsigned int* counter, bool reset_counter, int64_t max_n, int max_kept)
+                      unsigned int* counter, bool reset_counter, int64_t max_n, int max_kept, bool tensor = false,
+                      unsigned int* tc_counter = nullptr)
 {
     const DevSet& ds = ref ? c.set_ref : c.set;
     k_fold_sort<<<sm.slots, kFoldThreads, c.fold_smem, c.st>>>(ds, sm, c.dk);
@@ -2040,6 +2591,15 @@ gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weig
         const int bytes = buf * (int)(weighted ? sizeof(float2) : sizeof(float));
         k_window_tiles<<<c.n_sm * tiles::kCtasPerSm, tiles::kThreads, bytes, c.st>>>(ds, sm, c.dk, buf,
                                                                                    weighted ? 1 : 0, counter);
+        if (tensor && !weighted && tc_counter) {
+            // the durations marked kTensor (the tiled kernel gave them no tasks)
+            GTLS_CUDA(cudaGetLastError());
+            if (reset_counter) GTLS_CUDA(cudaMemsetAsync(tc_counter, 0, sizeof(unsigned int), c.st));
+            if (!c.tc_maps) return fail(GTLS_ERR_INTERNAL, "tensor-core window kernel without tensor maps");
+            k_window_tc<<<c.n_sm, tc::kThreads, tc::kSmemRequest, c.st>>>(ds, sm, c.dk, c.tc_maps, c.tc_jspan,
+                                                                        tc_counter, c.tc_test);
+            c.launches += 1;
+        }
     }
     if (!tiled || window_only) {
         // every duration, or (next to the tiled kernel) those marked kWindowOnly
@@ -2105,6 +2665,9 @@ SlotMap single_wave(int first, int cnt, int tiles_per_period, bool from_list)
 gtls_status check_words(const unsigned int* chk, const std::string& where)
 {
     if (chk[0] == 0) return GTLS_OK;
+    if (chk[0] == (unsigned int)tc::kCheckTimeout)
+        return fail(GTLS_ERR_TIMEOUT, where + "a tensor-core window kernel wait ran out (index " +
+                                          std::to_string(chk[1]) + ", wait " + std::to_string(chk[2]) + ")");
     return fail(GTLS_ERR_INTERNAL, where + "device index check " + std::to_string(chk[0]) + " failed (value " +
                                        std::to_string(((long long)chk[3] << 32) | chk[1]) + ", limit " +
                                        std::to_string(chk[2]) + ")");
@@ -2156,6 +2719,9 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
     c.median_blocks = (dp.np + median_outs(dp.median_half) - 1) / median_outs(dp.median_half);
     c.topk_smem = topk_smem_bytes(dp.np, pl->refine_k);
     c.st = st;
+    c.tc_jspan = pl->tc_jspan;
+    c.tc_test = pl->tc_test_wait;
+    c.tc_maps = pl->tc_maps;
     pl->profile = gtls_profile{};
     if (pl->profiling) c.prof = pl;
 
@@ -2175,7 +2741,7 @@ gtls_status run_search(gtls_plan* pl, const double* t, const double* y, const do
         const int cnt = std::min<int>(dk.chunk, dp.np - p0);
         GTLS_TRY(wave_pass(c, false, single_wave(p0, cnt, wtiled ? pl->tile_count_w : pl->tile_count, false),
                            tiled || wtiled, wtiled, tiled && pl->has_window_only, pl->tile_counter, true, n,
-                           h.max_kept));
+                           h.max_kept, tiled && pl->has_tensor, pl->tc_counter));
     }
     GTLS_TRY(sr_sde_pass(c));
     // two-stage T0 search (Sect. 2.5): the refine_k best periods by SDE(P)
@@ -2220,6 +2786,7 @@ struct BatchWave {
     bool tiled;
     bool weighted;
     bool window_only;   // some curve of the wave has durations marked kWindowOnly
+    bool tensor;        // some curve of the wave has durations marked kTensor
     bool ref;
     int64_t max_n;
     int max_kept;
@@ -2269,6 +2836,7 @@ struct gtls_batch {
     std::vector<uint8_t> fits, fits_ref;      // curve fits the tiled kernel at cfg.tile_buf
     std::vector<uint8_t> fits_w;              // ... with per-point weights at tile_buf_w pairs
     int tile_buf_w = 0;                       // (w r, w) pairs per tile of the weighted waves
+    const void* tc_maps = nullptr;            // TMA maps of dk.rs for the tensor-core window kernel
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
 };
@@ -2326,7 +2894,7 @@ void batch_tiles(gtls_batch* b, int buf)
         bool fits = true, fits1 = true;
         for (size_t j = 0; j < h.dpts.size(); ++j) {
             const int st = h.stride[j], d = h.dpts[j];
-            if (pl->variant_host[j] != tiles::kWindowOnly) {
+            if (pl->variant_host[j] != tiles::kWindowOnly && pl->variant_host[j] != tiles::kTensor) {
                 st_max = std::max(st_max, st);
                 dmax_t = std::max(dmax_t, d);
                 const int jrows = (d + st - 1) / st;
@@ -2367,6 +2935,7 @@ void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, 
         w.tiled = tiled;
         w.weighted = weighted;
         w.window_only = false;
+        w.tensor = false;
         w.ref = ref;
         w.sm.from_list = ref ? 1 : 0;
     };
@@ -2387,6 +2956,7 @@ void build_waves(const gtls_batch* b, const std::vector<Run>& runs, bool tiled, 
             w.max_kept = std::max(w.max_kept, h.max_kept);
             const gtls_plan* pl = b->plans[r.lc];
             if (tiled && !weighted && (ref ? pl->has_window_only_ref : pl->has_window_only)) w.window_only = true;
+            if (tiled && !weighted && !ref && pl->has_tensor) w.tensor = true;
             done += take;
         }
     }
@@ -2437,6 +3007,11 @@ Ctx batch_ctx(const gtls_batch* b, cudaStream_t st)
     c.median_blocks = b->median_blocks;
     c.topk_smem = b->topk_smem;
     c.st = st;
+    for (const gtls_plan* pl : b->plans) {
+        c.tc_jspan = std::max(c.tc_jspan, pl->tc_jspan);
+        c.tc_test = std::max(c.tc_test, pl->tc_test_wait);
+    }
+    c.tc_maps = b->tc_maps;
     return c;
 }
 
@@ -2447,11 +3022,12 @@ gtls_status batch_upload_tiles(gtls_batch* b)
     return GTLS_OK;
 }
 
-// Makes sure there is one window-kernel counter per tiled wave.
+// Makes sure there are two window-kernel counters (tiled, tensor-core) per
+// tiled wave.
 gtls_status batch_counters(gtls_batch* b, int tiled_waves)
 {
-    if (tiled_waves <= b->n_counters) return GTLS_OK;
-    const int n = std::max(tiled_waves, 2 * b->n_counters);
+    if (2 * tiled_waves <= b->n_counters) return GTLS_OK;
+    const int n = std::max(2 * tiled_waves, 2 * b->n_counters);
     GTLS_TRY(batch_alloc(b, &b->counters, n));
     b->n_counters = n;
     return GTLS_OK;
@@ -2461,11 +3037,13 @@ gtls_status batch_counters(gtls_batch* b, int tiled_waves)
 gtls_status batch_enqueue(gtls_batch* b, Ctx& c, const std::vector<BatchWave>& coarse,
                           const std::vector<BatchWave>& refine, int tiled_waves)
 {
-    GTLS_CUDA(cudaMemsetAsync(b->counters, 0, std::max(1, tiled_waves) * sizeof(unsigned int), c.st));
+    GTLS_CUDA(cudaMemsetAsync(b->counters, 0, 2 * std::max(1, tiled_waves) * sizeof(unsigned int), c.st));
     int ci = 0;
-    for (const BatchWave& w : coarse)
-        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, w.weighted, w.window_only, b->counters + (w.tiled ? ci++ : 0),
-                           false, w.max_n, w.max_kept));
+    for (const BatchWave& w : coarse) {
+        unsigned int* cnt = b->counters + 2 * (w.tiled ? ci++ : 0);
+        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, w.weighted, w.window_only, cnt, false, w.max_n, w.max_kept,
+                           w.tensor, cnt + 1));
+    }
     GTLS_TRY(sr_sde_pass(c));
     k_topk<<<c.n_lc, 1024, c.topk_smem, c.st>>>(c.set, 0);
     GTLS_CUDA(cudaGetLastError());
@@ -2473,7 +3051,7 @@ gtls_status batch_enqueue(gtls_batch* b, Ctx& c, const std::vector<BatchWave>& c
     if (!refine.empty()) {
         for (const BatchWave& w : refine)
             GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, w.weighted, w.window_only,
-                               b->counters + (w.tiled ? ci++ : 0), false, w.max_n, w.max_kept));
+                               b->counters + 2 * (w.tiled ? ci++ : 0), false, w.max_n, w.max_kept));
         GTLS_TRY(sr_sde_pass(c));
     }
     k_best<<<c.n_lc, 1024, 0, c.st>>>(c.set, 0, b->results, b->checks);
@@ -2644,6 +3222,16 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     GTLS_TRY(batch_alloc(b, &dk.ws, slots * pad_stride));
     GTLS_TRY(batch_alloc(b, &dk.wrs, slots * pad_stride));
     GTLS_TRY(batch_alloc(b, &dk.pf, slots * pad_stride));
+    {
+        bool any_tensor = false;
+        for (int i = 0; i < n_lc; ++i) any_tensor = any_tensor || plans[i]->has_tensor;
+        if (any_tensor) {
+            unsigned char* maps = nullptr;
+            GTLS_TRY(batch_alloc(b, &maps, (size_t)tc::kMaps * sizeof(CUtensorMap)));
+            GTLS_TRY(make_tc_maps(dk, maps));
+            b->tc_maps = maps;
+        }
+    }
 
     // per-curve descriptors
     std::vector<DevPlan> hp(2 * (size_t)n_lc);
@@ -2749,7 +3337,9 @@ gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, cons
                 if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = fail(GTLS_ERR_CUDA, "cudaEventRecord");
                 int ci = 0;
                 for (const BatchWave& w : waves) {
-                    s = wave_pass(c, false, w.sm, true, false, false, b->counters + ci++, true, w.max_n, w.max_kept);
+                    unsigned int* cnt = b->counters + 2 * ci++;
+                    s = wave_pass(c, false, w.sm, true, false, false, cnt, true, w.max_n, w.max_kept, w.tensor,
+                                  cnt + 1);
                     if (s != GTLS_OK) break;
                 }
             }

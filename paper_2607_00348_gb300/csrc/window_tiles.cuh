@@ -68,6 +68,7 @@ enum Variant : int {
     kCol8 = 9,
     kWeighted15 = 10,   // per-point weights: (w r, w) tile pairs x (s_k, s_k^2) template pairs
     kWindowOnly = 12,   // duration too long for a tile: the one-thread-per-window kernel takes it
+    kTensor = 13,       // uniform weights: the tensor-core kernel (window_tc.cuh) takes it
 };
 
 __host__ __device__ inline int variant_w(int v)

@@ -46,7 +46,7 @@ class PlanParams(ctypes.Structure):
                 ("u1", ctypes.c_double), ("u2", ctypes.c_double),
                 ("median_window", ctypes.c_int32), ("periods_per_chunk", ctypes.c_int32),
                 ("periods_days", c_double_p), ("n_periods", ctypes.c_int64),
-                ("refine_periods", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("refine_periods", ctypes.c_int32), ("test_flags", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -231,6 +231,7 @@ class PlanConfig:
     periods_per_chunk: int = 0
     refine_periods: int = 0
     periods_days: np.ndarray | None = None
+    test_flags: int = 0
 
 
 class Plan:
@@ -243,7 +244,7 @@ class Plan:
         for f in ("baseline_days", "n_points", "m_star", "r_star", "oversampling",
                   "period_min_days", "period_max_days", "k_min", "k_max", "q_cap",
                   "dur_ratio", "dt0", "u1", "u2", "median_window", "periods_per_chunk",
-                  "refine_periods"):
+                  "refine_periods", "test_flags"):
             v = getattr(cfg, f)
             setattr(prm, f, v if v is not None else 0)
         self._periods_in = None
