@@ -202,6 +202,12 @@ gtls_status gtls_search_host(gtls_plan* plan, const double* t, const double* y,
  * gtls_search.  Everything after the per-curve preparation is captured
  * once into a CUDA graph and replayed by later searches (recaptured when
  * the set of curves with uniform dy changes, or after gtls_batch_autotune).
+ * The periods of all curves form a device work queue of (curve, first,
+ * count) runs per kernel class; a while-loop node of the graph repeats
+ * {cut the next wave from the queue's cursor on the device, fold, window
+ * kernels, per-period results} until the queue is empty, so the graph's
+ * size does not depend on the number of curves or waves, and no kernel
+ * waits on another (stream order inside the loop body).
  * Results equal gtls_search on each curve alone.
  * Errors: INVALID_ARG (n_lc outside [1, 65535], null or repeated plans,
  * plans on another device), OOM, CUDA.
@@ -213,10 +219,11 @@ typedef struct gtls_batch_info {
     int64_t n_points;          /* all curves */
     int64_t n_periods;         /* trial periods of all curves (coarse pass) */
     double wpe;                /* window-point evaluations of all curves */
-    int32_t waves;             /* coarse waves of the captured graph (0 before the first search) */
+    int32_t waves;             /* waves (coarse and refinement) one search runs (0 before the first) */
     int32_t wave_slots;        /* periods per wave */
     int32_t tile_floats;       /* folded-curve floats staged per window-tile item */
-    int32_t graph_kernels;     /* kernels in the captured graph */
+    int32_t graph_kernels;     /* kernels in the captured graph, a loop body counted once: the same
+                                  for any number of curves of the same kernel classes */
     int64_t last_launches;     /* kernels launched by the last gtls_batch_search */
     int64_t device_bytes;      /* device memory owned by the batch */
     int32_t tuned;             /* 1 after gtls_batch_autotune */
@@ -272,6 +279,20 @@ gtls_status gtls_search_batch(gtls_plan* const* plans, int64_t n_lc,
                               const double* t, const double* y, const double* dy,
                               const int64_t* offsets, void* stream,
                               gtls_result* out);
+
+/*
+ * The plan's chunk scratch (the folded curves, prefix sums and sort keys of
+ * periods_per_chunk periods: plan info device_bytes counts it once it
+ * exists) is allocated by the first gtls_search on the plan.
+ * gtls_plan_reserve allocates it now (no-op when it exists);
+ * gtls_plan_trim frees it (it waits for the device; no-op when absent) and
+ * the next search allocates it again.  Many plans can then be kept for one
+ * search each without holding one scratch per plan.  Neither changes a
+ * result.  Errors: INVALID_ARG (null plan, another current device), OOM,
+ * CUDA.
+ */
+gtls_status gtls_plan_reserve(gtls_plan* plan);
+gtls_status gtls_plan_trim(gtls_plan* plan);
 
 /*
  * Measure per-stage device time with CUDA events on the search stream

@@ -184,7 +184,8 @@ struct gtls_plan {
     // one-entry device descriptor sets of the coarse and refinement passes
     gtls::DevSet set{}, set_ref{};
     int64_t* prep_off = nullptr;        // device {0, n}: the curve's offsets
-    bool chunk_ready = false;           // dk allocated (first single search)
+    bool chunk_ready = false;           // dk allocated (first single search or gtls_plan_reserve)
+    int64_t chunk_bytes = 0;            // device bytes of the chunk scratch
     std::vector<float> tmpl_pad;        // host copy of the zero-padded template table
     std::vector<int64_t> tmpl_pad_off;
     // stage profiling: events recorded on the search stream when enabled

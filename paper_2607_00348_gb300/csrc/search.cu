@@ -212,9 +212,11 @@ __device__ long long block_exclusive_scan1(long long v, long long* warp_sums, lo
 }
 
 // Light curve and period held by `slot` of a wave (segments ascend in
-// slot0); false when the period index is out of range.
+// slot0); false past the wave's slots or when the period index is out of
+// range.
 __device__ __forceinline__ bool resolve_slot(const DevSet& ds, const SlotMap& sm, int slot, int& lc, int& p)
 {
+    if (slot >= sm.slots) return false;
     int s = 0;
     while (s + 1 < sm.nseg && sm.seg[s + 1].slot0 <= slot) ++s;
     lc = sm.seg[s].lc;
@@ -608,9 +610,11 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             if (in_range32(dc.check, 7, lo + rank, len)) inv[lo + rank] = (uint16_t)q;
         }
         __syncthreads();
-        // gather in final-position order (kRankBatch points' loads in flight)
+        // gather in final-position order (kRankBatch points' loads in flight;
+        // batches past the super-bucket's length skipped, block-uniform)
 #pragma unroll
         for (int h = 0; h < kPerThread; h += kRankBatch) {
+            if ((uint32_t)h * kFoldThreads >= len) break;
             int32_t id[kRankBatch];
             bool ok[kRankBatch];
 #pragma unroll
@@ -832,8 +836,9 @@ __device__ void fold_global(unsigned char* smem, const DevPlan& dp, const DevCur
 }
 
 __global__ void __launch_bounds__(kFoldThreads, kFoldMinBlocks)
-k_fold_sort(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
+k_fold_sort(DevSet ds, const __grid_constant__ SlotMap smv, const SlotMap* smq, DevChunk dk)
 {
+    const SlotMap& sm = smq ? *smq : smv;
     extern __shared__ unsigned char smem[];
     const int slot_id = blockIdx.x;
     int lc, p;
@@ -886,8 +891,9 @@ __device__ __forceinline__ int kept_j(const DevPlan& dp, int p, int slot)
 }
 
 __global__ void __launch_bounds__(kSearchThreads)
-k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int only_window_only)
+k_window_search(DevSet ds, const __grid_constant__ SlotMap smv, const SlotMap* smq, DevChunk dk, int only_window_only)
 {
+    const SlotMap& sm = smq ? *smq : smv;
     __shared__ unsigned long long red[kSearchThreads / 32];
     const int slot_id = blockIdx.z;
     int lc, p;
@@ -952,9 +958,10 @@ k_window_search(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int 
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(tiles::kThreads, tiles::kCtasPerSm)
-k_window_tiles(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, int buf, int weighted,
+k_window_tiles(DevSet ds, const __grid_constant__ SlotMap smv, const SlotMap* smq, DevChunk dk, int buf, int weighted,
                unsigned int* counter)
 {
+    const SlotMap& sm = smq ? *smq : smv;
     using namespace tiles;
     extern __shared__ float tile_smem[];
     __shared__ DurTask dur[kMaxDur];
@@ -1538,9 +1545,10 @@ __device__ void tc_epilogue(const DevSet& ds, const SlotMap& sm, const DevChunk&
 }
 
 __global__ void __launch_bounds__(tc::kThreads, 1)
-k_window_tc(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, const void* maps, int jspan,
-            unsigned int* counter, int test_wait)
+k_window_tc(DevSet ds, const __grid_constant__ SlotMap smv, const SlotMap* smq, DevChunk dk, const void* maps,
+            int jspan, unsigned int* counter, int test_wait)
 {
+    const SlotMap& sm = smq ? *smq : smv;
     using namespace tc;
     extern __shared__ unsigned char tc_smem_raw[];
     __shared__ uint32_t s_tmem;
@@ -1594,8 +1602,9 @@ k_window_tc(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk, const vo
 // per-period result: chi2(P), depth, T0 of the minimum
 // ---------------------------------------------------------------------------
 
-__global__ void k_period_finalize(DevSet ds, const __grid_constant__ SlotMap sm, DevChunk dk)
+__global__ void k_period_finalize(DevSet ds, const __grid_constant__ SlotMap smv, const SlotMap* smq, DevChunk dk)
 {
+    const SlotMap& sm = smq ? *smq : smv;
     const int slot_id = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot_id >= sm.slots) return;
     int lc, p;
@@ -1624,6 +1633,69 @@ __global__ void k_period_finalize(DevSet ds, const __grid_constant__ SlotMap sm,
     dq.t0i[p] = (int32_t)s;
     dq.depth[p] = depth;
     dq.t0[p] = dc.scal[0] + ldexp((double)rho, -dp.time_exponent);
+}
+
+// ---------------------------------------------------------------------------
+// device work queue of the batched search: waves cut on the device
+// ---------------------------------------------------------------------------
+//
+// The periods of a batch are a list of (curve, first, count) runs; a wave
+// takes the next at most `wave_slots` periods of the list in at most kMaxSeg
+// segments.  k_wave_next cuts the next wave from the queue's cursor into
+// device memory, clears the wave's window-kernel counters and, when the
+// queue is empty after it, sets the condition of the enclosing graph loop to
+// zero, so that one loop node replays the wave kernels until the queue is
+// drained: the graph has the same nodes for any number of curves.
+
+struct QueueRun {
+    int32_t lc, first, count, tiles_pp;
+};
+
+struct WaveQueue {
+    const QueueRun* runs;
+    int32_t nruns;
+    int32_t wave_slots;
+    int32_t from_list;
+    int32_t* cursor;              // [0] run, [1] periods of that run taken, [2] waves cut
+    SlotMap* wave;                // the wave being searched
+    unsigned int* counters;       // the window kernels' item counters (2)
+    cudaGraphConditionalHandle cond;
+};
+
+__global__ void k_wave_next(WaveQueue q)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int r = q.cursor[0], off = q.cursor[1];
+    SlotMap& sm = *q.wave;
+    int nseg = 0, slots = 0, items = 0;
+    while (slots < q.wave_slots && nseg < kMaxSeg && r < q.nruns) {
+        const QueueRun u = q.runs[r];
+        const int take = min(u.count - off, q.wave_slots - slots);
+        sm.seg[nseg++] = WaveSeg{u.lc, u.first + off, slots, items};
+        slots += take;
+        items += take * u.tiles_pp;
+        off += take;
+        if (off >= u.count) {
+            ++r;
+            off = 0;
+        }
+    }
+    sm.nseg = nseg;
+    sm.slots = slots;
+    sm.items = items;
+    sm.from_list = q.from_list;
+    q.cursor[0] = r;
+    q.cursor[1] = off;
+    q.cursor[2] += 1;
+    q.counters[0] = 0;
+    q.counters[1] = 0;
+    cudaGraphSetConditional(q.cond, r < q.nruns ? 1u : 0u);
+}
+
+// Rewinds the cursors of `n` queues (3 words each).
+__global__ void k_queue_reset(int32_t* cursors, int n)
+{
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) cursors[i] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -2498,6 +2570,7 @@ gtls_status ensure_chunk(gtls_plan* pl)
     if (pl->chunk_ready) return GTLS_OK;
     DevChunk& dk = pl->dk;
     const int64_t chunk = dk.chunk;
+    const int64_t bytes0 = pl->device_bytes;
     GTLS_TRY(dev_alloc(pl, &dk.keys, chunk * dk.key_stride));
     GTLS_TRY(dev_alloc(pl, &dk.sidx, chunk * dk.fold_stride));
     GTLS_TRY(dev_alloc(pl, &dk.rs, chunk * dk.pad_stride));
@@ -2511,6 +2584,35 @@ gtls_status ensure_chunk(gtls_plan* pl)
         pl->tc_maps = maps;
     }
     pl->chunk_ready = true;
+    pl->chunk_bytes = pl->device_bytes - bytes0;
+    return GTLS_OK;
+}
+
+// Frees the chunk scratch.
+gtls_status trim_chunk(gtls_plan* pl)
+{
+    if (!pl->chunk_ready) return GTLS_OK;
+    GTLS_CUDA(cudaDeviceSynchronize());
+    const void* mine[] = {pl->dk.keys, pl->dk.sidx, pl->dk.rs, pl->dk.ws, pl->dk.wrs, pl->dk.pf, pl->tc_maps};
+    int kept = 0;
+    for (int i = 0; i < pl->n_allocs; ++i) {
+        bool chunk = false;
+        for (const void* m : mine) chunk = chunk || (m && m == pl->allocs[i]);
+        if (chunk) cudaFree(pl->allocs[i]);
+        else pl->allocs[kept++] = pl->allocs[i];
+    }
+    for (int i = kept; i < pl->n_allocs; ++i) pl->allocs[i] = nullptr;
+    pl->n_allocs = kept;
+    pl->device_bytes -= pl->chunk_bytes;
+    pl->chunk_bytes = 0;
+    const int32_t chunk = pl->dk.chunk;
+    pl->dk.keys = nullptr;
+    pl->dk.sidx = nullptr;
+    pl->dk.rs = pl->dk.ws = pl->dk.wrs = nullptr;
+    pl->dk.pf = nullptr;
+    pl->dk.chunk = chunk;
+    pl->tc_maps = nullptr;
+    pl->chunk_ready = false;
     return GTLS_OK;
 }
 
@@ -2577,26 +2679,29 @@ gtls_status stage_mark(Ctx& c, int stage)
 
 // One wave: fold + sort, every window, per-period results.  `counter` must
 // be zero when the window kernel starts (reset here when reset_counter).
+// With smq (a wave cut on the device, see k_wave_next) the kernels read the
+// wave from device memory; sm.slots then only sizes the grids (the most
+// slots a wave of the queue can hold).
 gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weighted, bool window_only,
                       unsigned int* counter, bool reset_counter, int64_t max_n, int max_kept, bool tensor = false,
-                      unsigned int* tc_counter = nullptr)
+                      unsigned int* tc_counter = nullptr, const SlotMap* smq = nullptr)
 {
     const DevSet& ds = ref ? c.set_ref : c.set;
-    k_fold_sort<<<sm.slots, kFoldThreads, c.fold_smem, c.st>>>(ds, sm, c.dk);
+    k_fold_sort<<<sm.slots, kFoldThreads, c.fold_smem, c.st>>>(ds, sm, smq, c.dk);
     GTLS_CUDA(cudaGetLastError());
     GTLS_TRY(stage_mark(c, kStageFold));
     if (tiled) {
         if (reset_counter) GTLS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c.st));
         const int buf = weighted ? c.tile_buf_w : c.tile_buf;
         const int bytes = buf * (int)(weighted ? sizeof(float2) : sizeof(float));
-        k_window_tiles<<<c.n_sm * tiles::kCtasPerSm, tiles::kThreads, bytes, c.st>>>(ds, sm, c.dk, buf,
+        k_window_tiles<<<c.n_sm * tiles::kCtasPerSm, tiles::kThreads, bytes, c.st>>>(ds, sm, smq, c.dk, buf,
                                                                                    weighted ? 1 : 0, counter);
         if (tensor && !weighted && tc_counter) {
             // the durations marked kTensor (the tiled kernel gave them no tasks)
             GTLS_CUDA(cudaGetLastError());
             if (reset_counter) GTLS_CUDA(cudaMemsetAsync(tc_counter, 0, sizeof(unsigned int), c.st));
             if (!c.tc_maps) return fail(GTLS_ERR_INTERNAL, "tensor-core window kernel without tensor maps");
-            k_window_tc<<<c.n_sm, tc::kThreads, tc::kSmemRequest, c.st>>>(ds, sm, c.dk, c.tc_maps, c.tc_jspan,
+            k_window_tc<<<c.n_sm, tc::kThreads, tc::kSmemRequest, c.st>>>(ds, sm, smq, c.dk, c.tc_maps, c.tc_jspan,
                                                                         tc_counter, c.tc_test);
             c.launches += 1;
         }
@@ -2605,7 +2710,7 @@ gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weig
         // every duration, or (next to the tiled kernel) those marked kWindowOnly
         dim3 grid((unsigned)((max_n + kSearchThreads - 1) / kSearchThreads), (unsigned)max_kept,
                   (unsigned)sm.slots);
-        k_window_search<<<grid, kSearchThreads, 0, c.st>>>(ds, sm, c.dk, tiled ? 1 : 0);
+        k_window_search<<<grid, kSearchThreads, 0, c.st>>>(ds, sm, smq, c.dk, tiled ? 1 : 0);
         if (tiled) {
             GTLS_CUDA(cudaGetLastError());
             c.launches += 1;
@@ -2613,7 +2718,7 @@ gtls_status wave_pass(Ctx& c, bool ref, const SlotMap& sm, bool tiled, bool weig
     }
     GTLS_CUDA(cudaGetLastError());
     GTLS_TRY(stage_mark(c, kStageWindow));
-    k_period_finalize<<<(sm.slots + 127) / 128, 128, 0, c.st>>>(ds, sm, c.dk);
+    k_period_finalize<<<(sm.slots + 127) / 128, 128, 0, c.st>>>(ds, sm, smq, c.dk);
     GTLS_CUDA(cudaGetLastError());
     GTLS_TRY(stage_mark(c, kStageFinalize));
     c.launches += 3;
@@ -2817,8 +2922,14 @@ struct gtls_batch {
     unsigned int* flags = nullptr;     // per curve validity flags
     unsigned int* checks = nullptr;    // 4 words per curve
     gtls_result* results = nullptr;
-    unsigned int* counters = nullptr;  // one per tiled wave
+    unsigned int* counters = nullptr;  // two per tiled wave (autotuner probes) or per graph loop
     int n_counters = 0;
+    // device work queues of the graph's loops: their (curve, first, count,
+    // tiles per period) runs, the wave each loop is searching and the cursors
+    int32_t* q_runs = nullptr;         // 4 words per run, at most 2 n_lc runs
+    gtls::SlotMap* q_waves = nullptr;  // kMaxLoops
+    int32_t* q_cursors = nullptr;      // 3 words per loop
+    cudaStream_t body_stream = nullptr;   // stream the loop bodies are captured on
     BatchCfg cfg;
     bool tuned = false;
     // graph of everything after the curve preparation, for one set of
@@ -2827,7 +2938,8 @@ struct gtls_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
-    int graph_kernels = 0;
+    int graph_kernels = 0;             // kernels in the graph (a loop body counted once)
+    int64_t graph_launches = 0;        // kernels one replay launches
     int waves = 0;
     int64_t last_launches = 0;         // kernels of the last search
     int64_t total_periods = 0;         // coarse plus refinement periods
@@ -2868,6 +2980,8 @@ void batch_release(gtls_batch* b)
     b->graph = nullptr;
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     b->cap_stream = nullptr;
+    if (b->body_stream) cudaStreamDestroy(b->body_stream);
+    b->body_stream = nullptr;
     for (void* p : b->allocs) cudaFree(p);
     b->allocs.clear();
 }
@@ -3022,50 +3136,149 @@ gtls_status batch_upload_tiles(gtls_batch* b)
     return GTLS_OK;
 }
 
-// Makes sure there are two window-kernel counters (tiled, tensor-core) per
-// tiled wave.
-gtls_status batch_counters(gtls_batch* b, int tiled_waves)
+// Makes sure there are two window-kernel counters (tiled, tensor-core) for
+// each of n waves or loops.
+gtls_status batch_counters(gtls_batch* b, int n)
 {
-    if (2 * tiled_waves <= b->n_counters) return GTLS_OK;
-    const int n = std::max(2 * tiled_waves, 2 * b->n_counters);
-    GTLS_TRY(batch_alloc(b, &b->counters, n));
-    b->n_counters = n;
+    if (2 * n <= b->n_counters) return GTLS_OK;
+    const int m = std::max(2 * n, 2 * b->n_counters);
+    GTLS_TRY(batch_alloc(b, &b->counters, m));
+    b->n_counters = m;
     return GTLS_OK;
 }
 
-// Everything after the curve preparation, for the given waves.
-gtls_status batch_enqueue(gtls_batch* b, Ctx& c, const std::vector<BatchWave>& coarse,
-                          const std::vector<BatchWave>& refine, int tiled_waves)
+// One loop of the batch graph: the runs of one kernel class, coarse or
+// refinement, and what its wave kernels need.
+constexpr int kMaxLoops = 6;   // classes 1, 2, 0 for the coarse and the refinement pass
+struct LoopSpec {
+    bool tiled = false, weighted = false, window_only = false, tensor = false, ref = false;
+    int64_t max_n = 0;
+    int max_kept = 0;
+    int run0 = 0, nruns = 0;   // runs[run0, run0 + nruns) of the queue table
+    int waves = 0;             // waves the device will cut (the host's build_waves count)
+    int body_kernels = 0;      // kernels per wave
+};
+
+void add_loop_spec(const gtls_batch* b, const std::vector<Run>& rs, bool tiled, bool weighted, bool ref,
+                   std::vector<QueueRun>& runs, std::vector<LoopSpec>& loops)
 {
-    GTLS_CUDA(cudaMemsetAsync(b->counters, 0, 2 * std::max(1, tiled_waves) * sizeof(unsigned int), c.st));
-    int ci = 0;
-    for (const BatchWave& w : coarse) {
-        unsigned int* cnt = b->counters + 2 * (w.tiled ? ci++ : 0);
-        GTLS_TRY(wave_pass(c, false, w.sm, w.tiled, w.weighted, w.window_only, cnt, false, w.max_n, w.max_kept,
-                           w.tensor, cnt + 1));
+    if (rs.empty()) return;
+    LoopSpec L;
+    L.tiled = tiled;
+    L.weighted = weighted;
+    L.ref = ref;
+    L.run0 = (int)runs.size();
+    for (const Run& r : rs) {
+        const gtls_plan* pl = b->plans[r.lc];
+        const DevTiles& tl = b->tiles_host[(ref ? b->n_lc : 0) + r.lc];
+        const int tiles_pp = tiled ? (weighted ? tl.count_w : tl.count) : 0;
+        runs.push_back(QueueRun{r.lc, r.first, r.count, tiles_pp});
+        L.max_n = std::max<int64_t>(L.max_n, pl->host.n);
+        L.max_kept = std::max(L.max_kept, pl->host.max_kept);
+        if (tiled && !weighted && (ref ? pl->has_window_only_ref : pl->has_window_only)) L.window_only = true;
+        if (tiled && !weighted && !ref && pl->has_tensor) L.tensor = true;
     }
+    L.nruns = (int)rs.size();
+    std::vector<BatchWave> w;
+    build_waves(b, rs, tiled, weighted, ref, b->cfg.wave_slots, w);
+    L.waves = (int)w.size();
+    loops.push_back(L);
+}
+
+// The loops of the graph in order (coarse classes 1, 2, 0, then the
+// refinement) and the queue table of their runs.
+void batch_loops(const gtls_batch* b, const std::vector<uint8_t>& cls, std::vector<QueueRun>& runs,
+                 std::vector<LoopSpec>& coarse, std::vector<LoopSpec>& refine)
+{
+    for (int k = 0; k < 3; ++k) {
+        const int klass = k == 2 ? 0 : k + 1;
+        std::vector<Run> rc, rr;
+        for (int i = 0; i < b->n_lc; ++i) {
+            const gtls_plan* pl = b->plans[i];
+            if (cls[i] == klass) rc.push_back(Run{i, 0, pl->dp.np});
+            const int klass_ref = (cls[i] == 1 && b->fits_ref[i]) ? 1 : 0;
+            if (pl->refine_k > 0 && klass_ref == klass) rr.push_back(Run{i, 0, pl->refine_k});
+        }
+        add_loop_spec(b, rc, klass != 0, klass == 2, false, runs, coarse);
+        add_loop_spec(b, rr, klass != 0, klass == 2, true, runs, refine);
+    }
+}
+
+// Appends, at the capture position of c.st, a while-loop node whose body
+// cuts the next wave of queue `qi` (k_wave_next) and searches it; the body
+// is captured on the batch's second stream.
+gtls_status capture_loop(gtls_batch* b, Ctx& c, LoopSpec& L, int qi)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    GTLS_CUDA(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !g) return fail(GTLS_ERR_INTERNAL, "batch graph capture is not active");
+    cudaGraphConditionalHandle h{};
+    GTLS_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};   // aggregate: every other byte zero
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    GTLS_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    GTLS_CUDA(cudaStreamUpdateCaptureDependencies(c.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+
+    WaveQueue q{};
+    q.runs = reinterpret_cast<const QueueRun*>(b->q_runs) + L.run0;
+    q.nruns = L.nruns;
+    q.wave_slots = b->cfg.wave_slots;
+    q.from_list = L.ref ? 1 : 0;
+    q.cursor = b->q_cursors + 3 * qi;
+    q.wave = b->q_waves + qi;
+    q.counters = b->counters + 2 * qi;
+    q.cond = h;
+    GTLS_CUDA(cudaStreamBeginCaptureToGraph(b->body_stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    Ctx cb = c;
+    cb.st = b->body_stream;
+    cb.launches = 0;
+    k_wave_next<<<1, 32, 0, cb.st>>>(q);
+    gtls_status s = cudaGetLastError() == cudaSuccess ? GTLS_OK : fail(GTLS_ERR_CUDA, "k_wave_next launch");
+    SlotMap grid{};   // grid sizes: the most slots a wave can hold
+    grid.slots = b->cfg.wave_slots;
+    if (s == GTLS_OK)
+        s = wave_pass(cb, L.ref, grid, L.tiled, L.weighted, L.window_only, q.counters, false, L.max_n, L.max_kept,
+                      L.tensor, q.counters + 1, q.wave);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->body_stream, &out);
+    if (s != GTLS_OK) return s;
+    if (e != cudaSuccess) return fail(GTLS_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(e));
+    L.body_kernels = (int)cb.launches + 1;
+    c.launches += L.body_kernels;
+    return GTLS_OK;
+}
+
+// Everything after the curve preparation: the coarse loops, SR / SDE and
+// the refinement list, the refinement loops, SR / SDE and the best
+// candidate of every curve.
+gtls_status batch_enqueue(gtls_batch* b, Ctx& c, std::vector<LoopSpec>& coarse, std::vector<LoopSpec>& refine)
+{
+    const int nloops = (int)(coarse.size() + refine.size());
+    k_queue_reset<<<1, 32, 0, c.st>>>(b->q_cursors, nloops);
+    GTLS_CUDA(cudaGetLastError());
+    c.launches += 1;
+    int qi = 0;
+    for (LoopSpec& L : coarse) GTLS_TRY(capture_loop(b, c, L, qi++));
     GTLS_TRY(sr_sde_pass(c));
     k_topk<<<c.n_lc, 1024, c.topk_smem, c.st>>>(c.set, 0);
     GTLS_CUDA(cudaGetLastError());
     c.launches += 1;
     if (!refine.empty()) {
-        for (const BatchWave& w : refine)
-            GTLS_TRY(wave_pass(c, true, w.sm, w.tiled, w.weighted, w.window_only,
-                               b->counters + 2 * (w.tiled ? ci++ : 0), false, w.max_n, w.max_kept));
+        for (LoopSpec& L : refine) GTLS_TRY(capture_loop(b, c, L, qi++));
         GTLS_TRY(sr_sde_pass(c));
     }
     k_best<<<c.n_lc, 1024, 0, c.st>>>(c.set, 0, b->results, b->checks);
     GTLS_CUDA(cudaGetLastError());
     c.launches += 1;
     return GTLS_OK;
-}
-
-int count_tiled(const std::vector<BatchWave>& a, const std::vector<BatchWave>& b)
-{
-    int n = 0;
-    for (const BatchWave& w : a) n += w.tiled ? 1 : 0;
-    for (const BatchWave& w : b) n += w.tiled ? 1 : 0;
-    return n;
 }
 
 gtls_status batch_capture(gtls_batch* b, cudaStream_t st, const std::vector<uint8_t>& cls)
@@ -3075,16 +3288,20 @@ gtls_status batch_capture(gtls_batch* b, cudaStream_t st, const std::vector<uint
     b->exec = nullptr;
     b->graph = nullptr;
     b->graph_class.clear();
-    std::vector<BatchWave> coarse, refine;
-    batch_waves(b, cls, b->cfg.wave_slots, coarse, refine);
-    const int tiled_waves = count_tiled(coarse, refine);
-    GTLS_TRY(batch_counters(b, tiled_waves));
+    std::vector<QueueRun> runs;
+    std::vector<LoopSpec> coarse, refine;
+    batch_loops(b, cls, runs, coarse, refine);
+    if (coarse.size() + refine.size() > (size_t)kMaxLoops || runs.size() > 2 * (size_t)b->n_lc)
+        return fail(GTLS_ERR_INTERNAL, "batch queue table overflow");
+    GTLS_TRY(batch_counters(b, kMaxLoops));
+    if (!runs.empty())
+        GTLS_CUDA(cudaMemcpy(b->q_runs, runs.data(), runs.size() * sizeof(QueueRun), cudaMemcpyHostToDevice));
     // captured on the batch's own stream (the caller's may be the legacy
     // default stream, which cannot be captured); launched on the caller's
     (void)st;
     Ctx c = batch_ctx(b, b->cap_stream);
     GTLS_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    gtls_status s = batch_enqueue(b, c, coarse, refine, tiled_waves);
+    gtls_status s = batch_enqueue(b, c, coarse, refine);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     if (s != GTLS_OK) {
@@ -3096,7 +3313,15 @@ gtls_status batch_capture(gtls_batch* b, cudaStream_t st, const std::vector<uint
     GTLS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
     b->graph_class = cls;
     b->graph_kernels = (int)c.launches;
-    b->waves = (int)coarse.size();
+    // kernels one replay launches: the fixed ones and every wave's body
+    int64_t per_search = c.launches, waves = 0;
+    for (const std::vector<LoopSpec>* v : {&coarse, &refine})
+        for (const LoopSpec& L : *v) {
+            per_search += (int64_t)(L.waves - 1) * L.body_kernels;
+            waves += L.waves;
+        }
+    b->graph_launches = per_search;
+    b->waves = (int)waves;
     return GTLS_OK;
 }
 
@@ -3153,7 +3378,7 @@ gtls_status batch_search(gtls_batch* b, const double* t, const double* y, const 
     GTLS_CUDA(cudaStreamSynchronize(st));
     for (int i = 0; i < b->n_lc; ++i)
         GTLS_TRY(check_words(&chk[4 * (size_t)i], "light curve " + std::to_string(i) + ": "));
-    b->last_launches = launches + b->graph_kernels;
+    b->last_launches = launches + b->graph_launches;
     return GTLS_OK;
 }
 
@@ -3162,6 +3387,7 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     if (n_lc < 1 || n_lc > 65535) return fail(GTLS_ERR_INVALID_ARG, "n_lc must be in [1, 65535]");
     GTLS_CUDA(cudaGetDevice(&b->device));
     GTLS_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    GTLS_CUDA(cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking));
     b->n_lc = (int)n_lc;
     b->plans.assign(plans, plans + n_lc);
     b->off.assign(1, 0);
@@ -3262,6 +3488,9 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     GTLS_TRY(batch_alloc(b, &b->flags, n_lc));
     GTLS_TRY(batch_alloc(b, &b->checks, 4 * (size_t)n_lc));
     GTLS_TRY(batch_alloc(b, &b->results, n_lc));
+    GTLS_TRY(batch_alloc(b, &b->q_runs, 4 * 2 * (size_t)n_lc));
+    GTLS_TRY(batch_alloc(b, &b->q_waves, (size_t)kMaxLoops));
+    GTLS_TRY(batch_alloc(b, &b->q_cursors, 3 * (size_t)kMaxLoops));
     b->total_periods = total_periods;
     batch_tiles(b, b->cfg.tile_buf);
     GTLS_TRY(batch_upload_tiles(b));
@@ -3608,6 +3837,26 @@ void gtls_plan_destroy(gtls_plan* pl)
     release(pl);
     if (switch_dev) cudaSetDevice(cur);
     delete pl;
+}
+
+gtls_status gtls_plan_reserve(gtls_plan* pl)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    g_last_error.clear();
+    int dev = -1;
+    GTLS_CUDA(cudaGetDevice(&dev));
+    if (dev != pl->device) return fail(GTLS_ERR_INVALID_ARG, "current device differs from the plan's device");
+    return ensure_chunk(pl);
+}
+
+gtls_status gtls_plan_trim(gtls_plan* pl)
+{
+    if (!pl) return fail(GTLS_ERR_INVALID_ARG, "null plan");
+    g_last_error.clear();
+    int dev = -1;
+    GTLS_CUDA(cudaGetDevice(&dev));
+    if (dev != pl->device) return fail(GTLS_ERR_INVALID_ARG, "current device differs from the plan's device");
+    return trim_chunk(pl);
 }
 
 gtls_status gtls_plan_set_profiling(gtls_plan* pl, int32_t on)

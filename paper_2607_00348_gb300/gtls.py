@@ -131,6 +131,8 @@ SIGNATURES = [
                                                      ctypes.c_void_p]),
     ("gtls_batch_destroy", None, [ctypes.c_void_p]),
     ("gtls_plan_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("gtls_plan_reserve", ctypes.c_int, [ctypes.c_void_p]),
+    ("gtls_plan_trim", ctypes.c_int, [ctypes.c_void_p]),
     ("gtls_plan_get_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     ("gtls_sr_sde_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -308,6 +310,20 @@ class Plan:
                                      y.ctypes.data_as(c_double_p), dy.ctypes.data_as(c_double_p),
                                      t.size, _stream_handle(stream), ctypes.byref(res)))
         return res
+
+    def device_bytes(self) -> int:
+        """Device memory the plan holds now (gtls_plan_get_info)."""
+        info = PlanInfo()
+        _check(_lib.gtls_plan_get_info(self.handle, ctypes.byref(info)))
+        return int(info.device_bytes)
+
+    def reserve(self):
+        """Allocate the chunk scratch now (gtls_plan_reserve)."""
+        _check(_lib.gtls_plan_reserve(self.handle))
+
+    def trim(self):
+        """Free the chunk scratch until the next search (gtls_plan_trim)."""
+        _check(_lib.gtls_plan_trim(self.handle))
 
     def set_profiling(self, on: bool = True):
         _check(_lib.gtls_plan_set_profiling(self.handle, 1 if on else 0))

@@ -1,5 +1,6 @@
 """Batched search (gtls_batch_*): many curves of uneven length in waves of a
-shared chunk scratch, replayed from a captured CUDA graph.
+shared chunk scratch, cut on the device from a work queue inside the loop
+nodes of a captured CUDA graph.
 
 Every result of a batch must equal the single-curve search of the same
 curve bit for bit (same kernels, same arithmetic per window), whatever the
@@ -74,7 +75,9 @@ def test_batch_equals_single_curve_searches():
         res = batch.search(t, y, dy, offs)
         _same(batch, plans, res, singles)
     info = batch.info()
-    assert info.waves > 1 and info.graph_kernels > 3 * info.waves
+    # waves are cut on the device inside loop nodes: the graph holds each
+    # loop body once, a replay launches it once per wave
+    assert info.waves > 1 and info.last_launches > info.graph_kernels
     assert info.n_lc == len(curves) and info.n_points == offs[-1]
     tuned = batch.autotune(t, y, dy, offs)
     assert tuned.tuned == 1 and tuned.tuned_flops > 0
@@ -157,3 +160,48 @@ def test_weighted_refinement_and_graph_recapture():
     batch.close()
     pl.close()
     pl2.close()
+
+
+def test_graph_does_not_grow_with_the_number_of_curves():
+    import paper_2607_00348_gb300 as pkg
+    # the same kernel class (uniform dy, tiled, no refinement) with two and
+    # with four curves: the same graph, more waves; results as searched alone
+    curves = _curves()[1:4] + [(lambda lc: (lc.t, lc.y, lc.dy, dict(lc.search)))(synth.short_white(seed=6))]
+    plans = _plans(curves)
+    infos = []
+    for sel in ([1, 2], [0, 1, 2, 3]):
+        sub = [curves[i] for i in sel]
+        t, y, dy, offs = _packed(sub)
+        batch = pkg.Batch([plans[i] for i in sel], wave_slots=600)
+        res = batch.search(t, y, dy, offs)
+        infos.append(batch.info())
+        batch.close()
+        for r, i in zip(res, sel):
+            rs, _ = gh.gpu_search(plans[i], curves[i][0], curves[i][1], curves[i][2])
+            assert r.as_dict() == rs.as_dict(), i
+    a, b = infos
+    assert a.graph_kernels == b.graph_kernels
+    assert b.waves > a.waves and b.last_launches > a.last_launches
+    for p in plans:
+        p.close()
+
+
+def test_trim_frees_the_chunk_scratch_and_search_reallocates_it():
+    lc = synth.short_white(seed=2)
+    pl = gh.plan_for(lc, lc.baseline_days, lc.search)
+    before = pl.device_bytes()
+    pl.reserve()
+    held = pl.device_bytes()
+    assert held > before
+    pl.reserve()   # no-op when it exists
+    assert pl.device_bytes() == held
+    r1, o1 = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    pl.trim()
+    assert pl.device_bytes() == before
+    pl.trim()      # no-op when absent
+    r2, o2 = gh.gpu_search(pl, lc.t, lc.y, lc.dy)
+    assert pl.device_bytes() == held
+    assert r1.as_dict() == r2.as_dict()
+    for k in ("chi2", "sde", "t0"):
+        assert np.array_equal(o1[k], o2[k]), k
+    pl.close()
