@@ -391,7 +391,7 @@ def learned_leg(args, lcs, plans, plain, dev):
 
     import paper_2607_00348_gb300 as pkg
     from paper_2607_00348_gb300 import proposal as pr
-    if not os.path.exists(pr.WEIGHTS):
+    if not pr.weights_match():
         return None
     params, meta = pr.load_weights()
     net = pkg.Cnn(len(lcs), params)

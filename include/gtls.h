@@ -70,7 +70,9 @@ typedef struct {
     double dt0;                 /* T0 step as a fraction of D (default 0.05) */
     double u1, u2;              /* quadratic limb darkening (default 0.4, 0.25) */
     int32_t median_window;      /* odd SDE median window; 0 => 2 floor(N_P/200) + 1 */
-    int32_t periods_per_chunk;  /* periods folded per kernel wave; 0 => fit 2 GiB of scratch */
+    int32_t periods_per_chunk;  /* periods folded per kernel wave; 0 => as many as fit 4 GiB of
+                                   scratch (at most 2048), rounded down to a multiple of the SM
+                                   count */
     const double* periods_days; /* optional explicit period grid (host, copied); NULL => Ofir */
     int64_t n_periods;          /* length of periods_days */
     int32_t refine_periods;     /* K > 0: re-search the K best periods by SDE(P) with T0 step 1
@@ -197,7 +199,8 @@ gtls_status gtls_search_host(gtls_plan* plan, const double* t, const double* y,
  * their own while the batch runs, since the batch writes their per-curve and
  * per-period buffers).  The batch owns one chunk scratch shared by all
  * curves (sized for the largest curve; `wave_slots` periods in flight, 0 =
- * as many as fit 8 GiB, at most 4096) and runs the periods of all curves as
+ * as many as fit 8 GiB, at most 4096, rounded down to a multiple of four
+ * times the SM count) and runs the periods of all curves as
  * waves of (curve, period range) segments through the same kernels as
  * gtls_search.  Everything after the per-curve preparation is captured
  * once into a CUDA graph and replayed by later searches (recaptured when
@@ -343,7 +346,9 @@ gtls_status gtls_sr_sde_noalloc(const double* chi2, int64_t n_periods, int32_t m
  * the whole grid when the prediction is not confident (caller's choice).
  *
  * Network: input x[B][4096]; six 'same' 1D convolutions (taps 7, 5, 5, 5,
- * 5, 5; 64 output channels) each with bias, ReLU and max-pooling by 2
+ * 5, 5 spaced 1, 2, 2, 4, 4, 8 bins of the layer's input apart:
+ * out[l] = b + sum_tap w[tap] x[l + (tap - (taps-1)/2) spacing]; 64 output
+ * channels) each with bias, ReLU and max-pooling by 2
  * (pair (2j, 2j+1), the first wins ties); a linear head from the 64 x 64
  * features (feature = position * 64 + channel) to 128 logits; scores =
  * sigmoid(logits).  Loss: masked mean logistic loss with soft targets,

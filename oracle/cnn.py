@@ -17,7 +17,7 @@ per-bin loop, Adam against its closed form after one step.
 
 Layouts (shared with the library's C ABI, which documents them too):
   activations  [batch][length][channels]   (channels contiguous)
-  conv weight  [out][tap][in]              (taps of width KS, 'same' padding)
+  conv weight  [out][tap][in]              (KS taps DIL bins apart, 'same' padding)
   head weight  [region][feature], feature = position * 64 + channel
 """
 
@@ -31,6 +31,7 @@ N_BINS = 4096
 CH = 64
 N_CONV = 6
 KS = (7, 5, 5, 5, 5, 5)        # taps of the six convolutions
+DIL = (1, 2, 2, 4, 4, 8)       # tap spacing (dilation) of each convolution, in its own input's bins
 N_REG = 128
 P_LO, P_HI = 0.5, 1024.0       # days: the regions split [P_LO, P_HI) evenly in log P
 
@@ -139,17 +140,17 @@ def init_params(seed, n_bins=N_BINS):
     return p
 
 
-def conv_same(x, w, b):
-    """out[n, l, o] = b[o] + sum_{k, i} w[o, k, i] x[n, l + k - (KS-1)/2, i]
+def conv_same(x, w, b, dil=1):
+    """out[n, l, o] = b[o] + sum_{k, i} w[o, k, i] x[n, l + (k - (KS-1)/2) dil, i]
     (zero outside 0..L-1)."""
     n, length, cin = x.shape
     cout, ks, _ = w.shape
-    pad = (ks - 1) // 2
+    pad = (ks - 1) // 2 * dil
     xp = np.zeros((n, length + 2 * pad, cin))
     xp[:, pad:pad + length] = x
     out = np.broadcast_to(b, (n, length, cout)).copy()
     for k in range(ks):
-        out += xp[:, k:k + length, :] @ w[:, k, :].T
+        out += xp[:, k * dil:k * dil + length, :] @ w[:, k, :].T
     return out
 
 
@@ -162,7 +163,7 @@ def forward(params, x, store=None):
     a = keep(np.asarray(x, np.float64))[:, :, None]
     cache = []
     for i in range(N_CONV):
-        pre = conv_same(a, params[f"w{i}"], params[f"b{i}"])
+        pre = conv_same(a, params[f"w{i}"], params[f"b{i}"], DIL[i])
         act = np.maximum(pre, 0.0)
         n, length, c = act.shape
         pair = act.reshape(n, length // 2, 2, c)
@@ -203,14 +204,16 @@ def backward(params, cache, dz):
         dpre = dpre.reshape(n, length, c) * (pre > 0)
         w = params[f"w{i}"]
         cout, ks, cin = w.shape
-        pad = (ks - 1) // 2
+        dil = DIL[i]
+        pad = (ks - 1) // 2 * dil
         xp = np.zeros((n, length + 2 * pad, cin))
         xp[:, pad:pad + length] = a_in
         gw = np.zeros_like(w)
         dxp = np.zeros_like(xp)
         for k in range(ks):
-            gw[:, k, :] = np.einsum("nlo,nli->oi", dpre, xp[:, k:k + length, :])
-            dxp[:, k:k + length, :] += dpre @ w[:, k, :]
+            sl = slice(k * dil, k * dil + length)
+            gw[:, k, :] = np.einsum("nlo,nli->oi", dpre, xp[:, sl, :])
+            dxp[:, sl, :] += dpre @ w[:, k, :]
         g[f"w{i}"] = gw
         g[f"b{i}"] = dpre.sum(axis=(0, 1))
         da = dxp[:, pad:pad + length, :]

@@ -4,8 +4,11 @@
 // is trained on spectra that the search itself produces).
 //
 // Network (fixed): input [B][4096][1]; six 'same' convolutions (taps 7, 5,
-// 5, 5, 5, 5; 64 channels) each followed by ReLU and max-pooling by 2;
-// linear head 4096 -> 128 regions; logistic loss with soft targets; Adam.
+// 5, 5, 5, 5, dilated 1, 2, 2, 4, 4, 8 bins of their own input; 64
+// channels) each followed by ReLU and max-pooling by 2; linear head 4096 ->
+// 128 regions; logistic loss with soft targets; Adam.  The dilations give
+// a last-layer unit a receptive field of about 1500 input bins (taps and
+// pooling windows; a third of the curve) instead of about 300.
 //
 // Every contraction (convolution forward, data and weight gradients, head
 // forward and its two gradients) runs through one BF16 tensor-core tile GEMM
@@ -51,6 +54,7 @@ constexpr int kConv = 6;
 constexpr int kReg = 128;
 constexpr int kFeat = (kBins >> kConv) * kCh;
 constexpr int kTaps[kConv] = {7, 5, 5, 5, 5, 5};
+constexpr int kDil[kConv] = {1, 2, 2, 4, 4, 8};   // tap spacing of each convolution (its input's bins)
 constexpr double kRegionLo = 0.5, kRegionHi = 1024.0;   // days: regions split this range evenly in log P
 
 // offsets of the flat parameter vector (order: w0 b0 ... w5 b5 wh bh)
@@ -94,12 +98,12 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // Operand views (value at (row, k); callers guarantee row and k in range)
 struct ConvIn {        // implicit im2col of x[B][L][C]: row = b L + l, k = tap C + c
     const bf16* x;
-    int L, C, pad;
+    int L, C, half, dil;   // taps at l + (tap - half) dil
     __device__ bf16 operator()(int row, int k) const
     {
         const int b = row / L, l = row - b * L;
         const int tap = k / C, c = k - tap * C;
-        const int src = l + tap - pad;
+        const int src = l + (tap - half) * dil;
         return (src >= 0 && src < L) ? x[((int64_t)b * L + src) * C + c] : __float2bfloat16(0.0f);
     }
 };
@@ -440,7 +444,7 @@ gtls_status cnn_forward(gtls_cnn* c, const float* x, int B, cudaStream_t st)
     PROP_CUDA(cudaGetLastError());
     for (int i = 0; i < kConv; ++i) {
         const int L = conv_len(i), cin = conv_cin(i), taps = kTaps[i];
-        ConvIn a{c->act[i], L, cin, (taps - 1) / 2};
+        ConvIn a{c->act[i], L, cin, (taps - 1) / 2, kDil[i]};
         RowMajor w{c->pb + c->lay.w[i], taps * cin};
         Epi ep{kEpiPoolRelu, nullptr, kCh, c->p + c->lay.b[i], c->act[i + 1], c->arg[i]};
         PROP_TRY(gemm(B * L, kCh, taps * cin, 0, a, w, ep, st));
@@ -482,7 +486,7 @@ gtls_status cnn_backward(gtls_cnn* c, const float* tgt, const float* mask, int B
         // dW[co][tap ci] = sum over positions of dpre[pos][co] x(pos, tap ci)
         {
             ColMajor a{c->dpre, kCh};
-            ConvInT b{ConvIn{c->act[i], L, cin, (taps - 1) / 2}};
+            ConvInT b{ConvIn{c->act[i], L, cin, (taps - 1) / 2, kDil[i]}};
             Epi ep{kEpiAtomic, c->g + c->lay.w[i], taps * cin, nullptr, nullptr, nullptr};
             PROP_TRY(gemm(kCh, taps * cin, (int)rows, 8192, a, b, ep, st));
         }
@@ -491,7 +495,7 @@ gtls_status cnn_backward(gtls_cnn* c, const float* tgt, const float* mask, int B
         if (i > 0) {
             // data gradient: 'same' convolution of dpre with the flipped,
             // transposed taps -> gradient of conv i-1's pooled output
-            ConvIn a{c->dpre, L, kCh, (taps - 1) / 2};
+            ConvIn a{c->dpre, L, kCh, (taps - 1) / 2, kDil[i]};
             FlippedW b{c->pb + c->lay.w[i], taps, cin, kCh};
             Epi ep{kEpiStore, c->da[cur ^ 1], cin, nullptr, nullptr, nullptr};
             PROP_TRY(gemm((int)rows, cin, taps * kCh, 0, a, b, ep, st));

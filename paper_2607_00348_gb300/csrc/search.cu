@@ -2227,9 +2227,17 @@ gtls_status create_device(gtls_plan* pl)
     dk.key_stride = std::max<int64_t>(dk.fold_stride, (int64_t)kFoldSegKeys << dp.fold_sb_log2);
     dk.pad_stride = (n + h.dmax + kPadMargin + 31) & ~int64_t(31);
     const int64_t per_period = dk.key_stride * 8 + dk.fold_stride * 4 + dk.pad_stride * (4 + 4 + 4 + 8);
-    const int64_t budget = int64_t(3) << 30;  // 3 GiB of chunk scratch
+    const int64_t budget = int64_t(4) << 30;  // 4 GiB of chunk scratch
     int64_t chunk = std::max<int64_t>(1, budget / per_period);
-    chunk = std::min<int64_t>(chunk, 1024);
+    chunk = std::min<int64_t>(chunk, 2048);
+    {
+        // whole waves of the fold (one CTA per period and SM): a multiple of
+        // the SM count when at least one wave fits
+        int dev = 0, sms = 0;
+        GTLS_CUDA(cudaGetDevice(&dev));
+        GTLS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (sms > 0 && chunk >= sms) chunk = chunk / sms * sms;
+    }
     if (h.prm.periods_per_chunk > 0) chunk = h.prm.periods_per_chunk;
     chunk = std::min<int64_t>(chunk, dp.np);
     dk.chunk = (int32_t)chunk;   // allocated by the first single-curve search
@@ -3438,6 +3446,7 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     const int64_t per_slot = key_stride * 8 + fold_stride * 4 + pad_stride * (4 + 4 + 4 + 8);
     const int64_t budget = int64_t(8) << 30;
     int64_t slots = std::min<int64_t>(4096, std::max<int64_t>(1, budget / per_slot));
+    if (b->n_sm > 0 && slots >= 4 * b->n_sm) slots = slots / (4 * b->n_sm) * (4 * b->n_sm);   // whole fold waves at 1, 1/2, 1/4
     if (wave_slots > 0) slots = wave_slots;
     b->max_slots = (int)slots;
     b->cfg.wave_slots = (int)slots;

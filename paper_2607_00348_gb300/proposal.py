@@ -40,6 +40,8 @@ import numpy as np
 from . import gtls as _g
 
 SDE_SCALE = 15.0
+TAPS = (7, 5, 5, 5, 5, 5)        # the network of libgtls (include/gtls.h)
+DILATION = (1, 2, 2, 4, 4, 8)
 FRAC = 0.05
 CHUNK = 256
 N_BINS = _g.N_BINS
@@ -151,7 +153,7 @@ def init_params(seed):
     rng = np.random.default_rng(seed)
     parts = []
     cin = 1
-    for taps in (7, 5, 5, 5, 5, 5):
+    for taps in TAPS:
         parts.append(rng.normal(0.0, math.sqrt(2.0 / (taps * cin)), 64 * taps * cin))
         parts.append(np.zeros(64))
         cin = 64
@@ -244,21 +246,22 @@ def detected(res, inj, sde_min=9.0, rel=0.01):
     return res.sde >= sde_min and abs(res.period - inj["period"]) / inj["period"] < rel
 
 
-def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verify_sde=None):
+def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verify_sde=None,
+             verify_taus=()):
     """Recall (SDE >= 9, period within 1 %) and light curves per hour of the
-    plain batched search and of the proposal search at every tau, on curves
-    0 .. n_eval-1 of sequence `seed`; per curve, the injection, the plain
-    result and the network's largest region score."""
+    plain batched search and of the proposal search at every tau (and, with
+    verify_sde, at every tau of verify_taus with the verification fallback),
+    on curves 0 .. n_eval-1 of sequence `seed`; per curve, the injection, the
+    plain result and the network's largest region score."""
     import torch
     curves = [c for ch in curve_chunks(seed, n_eval, pool) for c in ch]
     full = [plan_for(c[0].size, c[4]) for c in curves]
     t, y, dy, offs = _pack(curves, dev)
     batch = _g.Batch(full)
     batch.autotune(t, y, dy, offs)
-    batch.search(t, y, dy, offs)                # graph capture
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    plain = batch.search(t, y, dy, offs)
+    plain = batch.search(t, y, dy, offs)        # includes the graph capture (milliseconds)
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - w0
     batch.close()
@@ -278,13 +281,15 @@ def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verif
                           "plain_sde": r.sde, "plain_detected": bool(detected(r, c[3])),
                           "score_max": float(sc[i][mask > 0].max())})
     out["per_curve"] = per_curve
-    for tau in taus:
+    runs = [(tau, None) for tau in taus] + [(tau, verify_sde) for tau in verify_taus if verify_sde]
+    for tau, vs in runs:
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        res, fb, searched = proposal_search(net, curves, full, dev, tau, frac, verify_sde)
+        res, fb, searched = proposal_search(net, curves, full, dev, tau, frac, vs)
         torch.cuda.synchronize()
         s = time.perf_counter() - w0
-        row = {"tau": tau, "recall": sum(detected(r, i) for r, i in zip(res, inj)) / max(n_inj, 1),
+        row = {"tau": tau, "verify_sde": vs,
+               "recall": sum(detected(r, i) for r, i in zip(res, inj)) / max(n_inj, 1),
                "false_alarms": sum(1 for r, i in zip(res, inj) if not i and r.sde >= 9.0),
                "fallback": int(sum(fb)), "periods_searched": int(sum(searched)),
                "periods_total": int(sum(p.n_periods for p in full)),
@@ -295,6 +300,15 @@ def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verif
     for p in full:
         p.close()
     return out
+
+
+def weights_match(path=WEIGHTS):
+    """True when `path` exists and holds weights of this network (taps and
+    dilations)."""
+    if not os.path.exists(path):
+        return False
+    _, meta = load_weights(path)
+    return tuple(meta.get("taps", ())) == TAPS and tuple(meta.get("dilation", ())) == DILATION
 
 
 def load_weights(path=WEIGHTS):
@@ -324,6 +338,8 @@ def main(argv=None):
     ev.add_argument("--taus", default="0.0,0.3,0.5")
     ev.add_argument("--frac", type=float, default=FRAC)
     ev.add_argument("--verify-sde", type=float, default=None)
+    ev.add_argument("--verify-taus", default="",
+                    help="taus evaluated again with the --verify-sde fallback")
     ev.add_argument("--json", default=None)
     ev.add_argument("--workers", type=int, default=8)
     a = ap.parse_args(argv)
@@ -343,7 +359,8 @@ def main(argv=None):
         t_train = time.time() - t0
         meta = {"train_curves": a.train, "seed": a.seed, "epochs": a.epochs, "batch": a.batch,
                 "lr": a.lr, "loss": hist, "data_seconds": t_data, "train_seconds": t_train,
-                "sde_scale": SDE_SCALE, "target": "binned-curve TLS (oversampling 1) region SDE"}
+                "sde_scale": SDE_SCALE, "target": "binned-curve TLS (oversampling 1) region SDE",
+                "taps": list(TAPS), "dilation": list(DILATION)}
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
         np.savez_compressed(a.out, params=net.params(), meta=json.dumps(meta))
         log(json.dumps({k: v for k, v in meta.items() if k != "loss"}))
@@ -352,8 +369,9 @@ def main(argv=None):
         params, meta = load_weights(a.weights)
         net = _g.Cnn(max(a.eval, 1), params)
         taus = [float(v) for v in a.taus.split(",")]
+        vtaus = [float(v) for v in a.verify_taus.split(",") if v.strip()]
         out = evaluate(net, a.eval, a.seed, dev, taus, frac=a.frac, pool=pool, log=log,
-                       verify_sde=a.verify_sde)
+                       verify_sde=a.verify_sde, verify_taus=vtaus)
         out["weights"] = {k: v for k, v in meta.items() if k != "loss"}
         print(json.dumps(out))
         if a.json:

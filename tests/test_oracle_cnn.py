@@ -24,6 +24,17 @@ def test_conv_same_equals_numpy_convolve():
         np.testing.assert_allclose(out, np.convolve(x, w[::-1], mode="same"), rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("ks,dil", [(5, 2), (5, 8), (7, 3)])
+def test_dilated_conv_equals_numpy_convolve_of_the_zero_stuffed_taps(ks, dil):
+    rng = np.random.default_rng(ks * 10 + dil)
+    x = rng.normal(size=61)
+    w = rng.normal(size=ks)
+    stuffed = np.zeros((ks - 1) * dil + 1)
+    stuffed[::dil] = w
+    out = cnn.conv_same(x[None, :, None], w[None, :, None], np.zeros(1), dil)[0, :, 0]
+    np.testing.assert_allclose(out, np.convolve(x, stuffed[::-1], mode="same"), rtol=1e-12, atol=1e-12)
+
+
 def test_conv_same_sums_input_channels_and_adds_bias():
     rng = np.random.default_rng(1)
     x = rng.normal(size=(2, 16, 3))
