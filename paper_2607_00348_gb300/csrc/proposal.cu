@@ -7,8 +7,8 @@
 // 5, 5, 5, 5, dilated 1, 2, 2, 4, 4, 8 bins of their own input; 64
 // channels) each followed by ReLU and max-pooling by 2; linear head 4096 ->
 // 128 regions; logistic loss with soft targets; Adam.  The dilations give
-// a last-layer unit a receptive field of about 1500 input bins (taps and
-// pooling windows; a third of the curve) instead of about 300.
+// a last-layer unit a receptive field of about 1530 input bins (taps and
+// pooling windows; more than a third of the curve) instead of about 320.
 //
 // Every contraction (convolution forward, data and weight gradients, head
 // forward and its two gradients) runs through one BF16 tensor-core tile GEMM

@@ -560,7 +560,7 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
 #pragma unroll
         for (int u = 0; u < kPerThread; ++u) {
             const uint32_t q = threadIdx.x + u * kFoldThreads;
-            kv[u] = q < len ? region[q] : 0ull;
+            kv[u] = q < len ? __ldcs(region + q) : 0ull;   // last use of the staged key
         }
 #pragma unroll
         for (int u = 0; u < kPerThread; ++u) {
@@ -636,12 +636,15 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
                 const uint32_t i = threadIdx.x + (h + j) * kFoldThreads;
                 if (!ok[j]) continue;
                 const int64_t g = (int64_t)k0 + i;
-                o.sidx[g] = id[j];
-                o.rs[g] = pv[j].r;
+                // streaming stores: the window kernels read the folded curve
+                // after the whole chunk is folded, from DRAM, so these lines
+                // go first when L2 needs room (the super-bucket regions stay)
+                __stcs(o.sidx + g, id[j]);
+                __stcs(o.rs + g, pv[j].r);
                 srfx[swz(i)] = pv[j].rfx;
                 if (!o.uniform) {
-                    o.ws[g] = pv[j].w;
-                    o.wrs[g] = pv[j].w * pv[j].r;
+                    __stcs(o.ws + g, pv[j].w);
+                    __stcs(o.wrs + g, pv[j].w * pv[j].r);
                 }
             }
         }
@@ -665,7 +668,7 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             carry += sum;
         }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) o.pf[(int64_t)k0 + 1 + i] = srfx[swz(i)];
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) __stcs(o.pf + (int64_t)k0 + 1 + i, srfx[swz(i)]);
         __syncthreads();   // the next super-bucket overwrites the staged keys and rfx
     }
     return true;

@@ -272,7 +272,11 @@ def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verif
                      "false_alarms": sum(1 for r, i in zip(plain, inj) if not i and r.sde >= 9.0),
                      "seconds": plain_s, "lc_per_hour": n_eval * 3600.0 / plain_s},
            "verify_sde": verify_sde, "learned": []}
-    sc = scores_for(net, curves, dev)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    sc = scores_for(net, curves, dev)     # binning + network forward of every curve
+    torch.cuda.synchronize()
+    out["network_seconds"] = time.perf_counter() - w0
     per_curve = []
     for i, (c, r) in enumerate(zip(curves, plain)):
         _, mask = _g.region_targets(full[i].periods(), np.zeros(full[i].n_periods))
@@ -281,6 +285,7 @@ def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verif
                           "plain_sde": r.sde, "plain_detected": bool(detected(r, c[3])),
                           "score_max": float(sc[i][mask > 0].max())})
     out["per_curve"] = per_curve
+    out["triage"] = triage(per_curve, out["plain"]["lc_per_hour"])
     runs = [(tau, None) for tau in taus] + [(tau, verify_sde) for tau in verify_taus if verify_sde]
     for tau, vs in runs:
         torch.cuda.synchronize()
@@ -309,6 +314,34 @@ def weights_match(path=WEIGHTS):
         return False
     _, meta = load_weights(path)
     return tuple(meta.get("taps", ())) == TAPS and tuple(meta.get("dilation", ())) == DILATION
+
+
+def triage(per_curve, plain_lc_per_hour):
+    """Curve triage by the network's largest region score, cross-validated on
+    the two halves of the evaluation set: the score threshold that keeps every
+    plain detection of one half is applied to the other half, whose curves
+    below it are not searched at all.  Returns one row per direction: curves
+    searched, plain detections kept, recall against plain recall, and the
+    light curves per hour of the plain search divided by the fraction of
+    curves searched (the network's own cost is reported separately)."""
+    n = len(per_curve)
+    score = np.array([c["score_max"] for c in per_curve])
+    det = np.array([bool(c["plain_detected"]) for c in per_curve])
+    inj = np.array([c["inj_period"] is not None for c in per_curve])
+    first = np.arange(n) < n // 2
+    rows = []
+    for cal, test in ((first, ~first), (~first, first)):
+        if not (cal & det).any():
+            continue
+        thr = float(score[cal & det].min())
+        keep = test & (score >= thr)
+        frac = keep.sum() / max(test.sum(), 1)
+        rows.append({"threshold": thr, "curves": int(test.sum()), "searched": int(keep.sum()),
+                     "detections_kept": int((keep & det).sum()), "detections_plain": int((test & det).sum()),
+                     "recall": float((keep & det).sum() / max((test & inj).sum(), 1)),
+                     "recall_plain": float((test & det).sum() / max((test & inj).sum(), 1)),
+                     "lc_per_hour": float(plain_lc_per_hour / max(frac, 1e-9))})
+    return rows
 
 
 def load_weights(path=WEIGHTS):

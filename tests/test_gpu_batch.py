@@ -205,3 +205,27 @@ def test_trim_frees_the_chunk_scratch_and_search_reallocates_it():
     for k in ("chi2", "sde", "t0"):
         assert np.array_equal(o1[k], o2[k]), k
     pl.close()
+
+
+def test_many_short_grids_fill_waves_up_to_the_segment_limit():
+    # 40 curves with short explicit grids (11 to 50 periods each): a wave of
+    # 4096 slots holds at most 32 (curve, period range) segments, so the
+    # device cuts a wave at the segment limit before it is full, then carries
+    # on with the next curves; every result equals the curve searched alone
+    import paper_2607_00348_gb300 as pkg
+    curves, plans = [], []
+    for s in range(40):
+        lc = synth.short_white(seed=100 + s)
+        periods = np.geomspace(0.7, 9.0, 11 + s)
+        curves.append((lc.t, lc.y, lc.dy, dict(periods_days=periods)))
+        plans.append(gh.plan_for(lc.n, lc.baseline_days, periods_days=periods))
+    t, y, dy, offs = _packed(curves)
+    batch = pkg.Batch(plans, wave_slots=4096)
+    res = batch.search(t, y, dy, offs)
+    info = batch.info()
+    assert info.waves == 2      # 32 segments, then the last 8 curves
+    singles = [gh.gpu_search(p, c[0], c[1], c[2]) for p, c in zip(plans, curves)]
+    _same(batch, plans, res, singles)
+    batch.close()
+    for p in plans:
+        p.close()
