@@ -70,8 +70,8 @@ typedef struct {
     double dt0;                 /* T0 step as a fraction of D (default 0.05) */
     double u1, u2;              /* quadratic limb darkening (default 0.4, 0.25) */
     int32_t median_window;      /* odd SDE median window; 0 => 2 floor(N_P/200) + 1 */
-    int32_t periods_per_chunk;  /* periods folded per kernel wave; 0 => as many as fit 4 GiB of
-                                   scratch (at most 2048), rounded down to a multiple of the SM
+    int32_t periods_per_chunk;  /* periods folded per kernel wave; 0 => as many as fit 8 GiB of
+                                   scratch (at most 4096), rounded down to a multiple of the SM
                                    count */
     const double* periods_days; /* optional explicit period grid (host, copied); NULL => Ofir */
     int64_t n_periods;          /* length of periods_days */

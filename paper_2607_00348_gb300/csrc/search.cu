@@ -571,6 +571,15 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
             if (q < len) atomicAdd(&fcnt[f], 1u);
         }
         __syncthreads();
+        // every staged key of the super-bucket is in registers now: drop the
+        // region's lines from L2 without writing them back (the next period
+        // writes the region again before reading it), so that the keys
+        // cost no DRAM traffic when they stayed in L2
+        {
+            const uint32_t lines = (len * (uint32_t)sizeof(unsigned long long) + 127u) / 128u;
+            for (uint32_t l = threadIdx.x; l < lines; l += blockDim.x)
+                asm volatile("discard.global.L2 [%0], 128;" ::"l"(region + 16 * l) : "memory");
+        }
         {
             constexpr int kPer = (1 << kFoldFineLog2) / kFoldThreads;
             const int f0 = threadIdx.x * kPer;
@@ -2230,9 +2239,11 @@ gtls_status create_device(gtls_plan* pl)
     dk.key_stride = std::max<int64_t>(dk.fold_stride, (int64_t)kFoldSegKeys << dp.fold_sb_log2);
     dk.pad_stride = (n + h.dmax + kPadMargin + 31) & ~int64_t(31);
     const int64_t per_period = dk.key_stride * 8 + dk.fold_stride * 4 + dk.pad_stride * (4 + 4 + 4 + 8);
-    const int64_t budget = int64_t(4) << 30;  // 4 GiB of chunk scratch
+    // 8 GiB of chunk scratch (measured on the Kepler-like search: 1024,
+    // 1520 and 3040 periods per chunk took 1013, 994 and 980 ms)
+    const int64_t budget = int64_t(8) << 30;
     int64_t chunk = std::max<int64_t>(1, budget / per_period);
-    chunk = std::min<int64_t>(chunk, 2048);
+    chunk = std::min<int64_t>(chunk, 4096);
     {
         // whole waves of the fold (one CTA per period and SM): a multiple of
         // the SM count when at least one wave fits
