@@ -199,7 +199,7 @@ gtls_status gtls_search_host(gtls_plan* plan, const double* t, const double* y,
  * their own while the batch runs, since the batch writes their per-curve and
  * per-period buffers).  The batch owns one chunk scratch shared by all
  * curves (sized for the largest curve; `wave_slots` periods in flight, 0 =
- * as many as fit 8 GiB, at most 4096, rounded down to a multiple of four
+ * as many as fit 16 GiB, at most 4096, rounded down to a multiple of four
  * times the SM count) and runs the periods of all curves as
  * waves of (curve, period range) segments through the same kernels as
  * gtls_search.  Everything after the per-curve preparation is captured

@@ -3458,7 +3458,7 @@ gtls_status batch_create(gtls_plan* const* plans, int64_t n_lc, int32_t wave_slo
     dk.key_stride = key_stride;
     dk.pad_stride = pad_stride;
     const int64_t per_slot = key_stride * 8 + fold_stride * 4 + pad_stride * (4 + 4 + 4 + 8);
-    const int64_t budget = int64_t(8) << 30;
+    const int64_t budget = int64_t(16) << 30;
     int64_t slots = std::min<int64_t>(4096, std::max<int64_t>(1, budget / per_slot));
     if (b->n_sm > 0 && slots >= 4 * b->n_sm) slots = slots / (4 * b->n_sm) * (4 * b->n_sm);   // whole fold waves at 1, 1/2, 1/4
     if (wave_slots > 0) slots = wave_slots;

@@ -240,6 +240,39 @@ def proposal_search(net, curves, full_plans, dev, tau, frac=FRAC, verify_sde=Non
     return res, fallback, searched
 
 
+def triage_search(net, curves, full_plans, dev, threshold, scores=None):
+    """Search, on its whole grid, every curve whose largest region score
+    reaches `threshold`; skip the others.  Returns (results with None for a
+    skipped curve, number of curves searched)."""
+    sc = scores_for(net, curves, dev) if scores is None else scores
+    keep = []
+    for i, fp in enumerate(full_plans):
+        per = fp.periods()
+        _, mask = _g.region_targets(per, np.zeros(per.size))
+        conf = float(sc[i][mask > 0].max()) if mask.any() else 0.0
+        if conf >= threshold:
+            keep.append(i)
+    res = [None] * len(curves)
+    if keep:
+        t, y, dy, offs = _pack([curves[i] for i in keep], dev)
+        batch = _g.Batch([full_plans[i] for i in keep])
+        for i, r in zip(keep, batch.search(t, y, dy, offs)):
+            res[i] = r
+        batch.close()
+    return res, len(keep)
+
+
+def triage_threshold(path=None):
+    """The smaller of the two cross-validated triage thresholds of the
+    evaluation record next to the weights (None without one)."""
+    path = path or os.path.join(os.path.dirname(WEIGHTS), "proposal_eval.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rows = json.load(f).get("triage") or []
+    return min(r["threshold"] for r in rows) if rows else None
+
+
 def detected(res, inj, sde_min=9.0, rel=0.01):
     if not inj:
         return False
