@@ -3111,24 +3111,6 @@ std::vector<uint8_t> batch_classes(const gtls_batch* b, const std::vector<unsign
     return c;
 }
 
-void batch_waves(const gtls_batch* b, const std::vector<uint8_t>& cls, int wave_slots,
-                 std::vector<BatchWave>& coarse, std::vector<BatchWave>& refine)
-{
-    for (int k = 0; k < 3; ++k) {   // classes 1, 2, 0
-        const int klass = k == 2 ? 0 : k + 1;
-        std::vector<Run> runs, runs_ref;
-        for (int i = 0; i < b->n_lc; ++i) {
-            const gtls_plan* pl = b->plans[i];
-            if (cls[i] == klass) runs.push_back(Run{i, 0, pl->dp.np});
-            // refinement: tiled only with uniform weights, else one thread per window
-            const int klass_ref = (cls[i] == 1 && b->fits_ref[i]) ? 1 : 0;
-            if (pl->refine_k > 0 && klass_ref == klass) runs_ref.push_back(Run{i, 0, pl->refine_k});
-        }
-        build_waves(b, runs, klass != 0, klass == 2, false, wave_slots, coarse);
-        build_waves(b, runs_ref, klass != 0, klass == 2, true, wave_slots, refine);
-    }
-}
-
 Ctx batch_ctx(const gtls_batch* b, cudaStream_t st)
 {
     Ctx c;
