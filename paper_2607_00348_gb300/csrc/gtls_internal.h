@@ -20,7 +20,7 @@ struct DevPlan {
     int32_t time_exponent;
     int32_t idx_bits;
     int32_t bucket_log2;
-    int32_t fold_sb_log2;  // super-buckets of the staged fold (log2)
+    int32_t fold_nsb;      // super-buckets of the staged fold
     int32_t max_kept;
     const double* periods;
     const int64_t* p_lat;

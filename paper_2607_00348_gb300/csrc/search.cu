@@ -352,8 +352,10 @@ __global__ void k_curve_reduce(const double* __restrict__ dy, const int64_t* __r
 //
 // The folded order is the order of the keys (rho << idx_bits | i).  Two
 // monotone functions of rho split it into buckets: fold_bucket (2^bucket_log2
-// buckets) and fold_fine (2^(sb_log2 + kFoldFineLog2) fine buckets, grouped
-// into 2^sb_log2 super-buckets of 2^kFoldFineLog2 each).
+// buckets) and fold_fine (nsb 2^kFoldFineLog2 fine buckets, grouped into nsb
+// super-buckets of 2^kFoldFineLog2 each; nsb is chosen so that a
+// super-bucket holds about kFoldFillKeys points, three quarters of its
+// region, on average).
 //
 // Staged path (the common case): the keys are scattered once into global
 // memory, each into its super-bucket's region of kFoldSegKeys slots -- a few
@@ -366,10 +368,14 @@ __global__ void k_curve_reduce(const double* __restrict__ dy, const int64_t* __r
 
 constexpr int kFoldFineLog2 = 11;   // fine buckets per super-bucket (log2)
 constexpr int kFoldMaxSbLog2 = 10;  // at most one super-bucket per fold thread
+constexpr int kFoldFillKeys = 6144; // mean points per super-bucket the plan aims at
 
-__device__ __forceinline__ uint32_t fold_fine(long long rho, int sh, uint32_t mul, int fshift)
+// Fine bucket of phase rho: floor((rho >> sh) mulf / 2^32) with
+// mulf = floor(nsb 2^(kFoldFineLog2 + 32) / top), top > rho >> sh, is
+// monotone in rho and below nsb 2^kFoldFineLog2.
+__device__ __forceinline__ uint32_t fold_fine(long long rho, int sh, uint32_t mulf)
 {
-    return (uint32_t)((((unsigned long long)rho >> sh) * (unsigned long long)mul) >> fshift);
+    return (uint32_t)((((unsigned long long)rho >> sh) * (unsigned long long)mulf) >> 32);
 }
 
 struct FoldOut {
@@ -468,12 +474,11 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
     const long long P = dp.p_lat[p];
     const float inv_p = dp.inv_p[p];
     const int sh = dp.bucket_shift[p];
-    const uint32_t mul = dp.bucket_mul[p];
     const int ib = dp.idx_bits;
     const unsigned long long idx_mask = (1ull << ib) - 1ull;
-    const int sb_log2 = dp.fold_sb_log2;
-    const int nsb = 1 << sb_log2;
-    const int fshift = dp.bucket_log2 + 32 - (sb_log2 + kFoldFineLog2);
+    const int nsb = dp.fold_nsb;
+    const uint32_t mulf = (uint32_t)(((unsigned long long)nsb << (kFoldFineLog2 + 32)) /
+                                     (((unsigned long long)P >> sh) + 1ull));
     constexpr uint32_t kFineMask = (1u << kFoldFineLog2) - 1u;
     static_assert((1 << kFoldFineLog2) % kFoldThreads == 0, "fine buckets split evenly over the threads");
     static_assert((1 << kFoldMaxSbLog2) <= kFoldThreads, "one super-bucket count per thread");
@@ -512,7 +517,7 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
         for (int u = 0; u < kFoldUnroll; ++u) {
             const int64_t i = g0 + u * bs + threadIdx.x;
             const long long rho = lattice_rho(dl[u], df[u], P, inv_p);
-            const uint32_t sb = fold_fine(rho, sh, mul, fshift) >> kFoldFineLog2;
+            const uint32_t sb = fold_fine(rho, sh, mulf) >> kFoldFineLog2;
             const bool ok = i < n && in_range(dc.check, 2, rho, P) && in_range32(dc.check, 1, sb, nsb);
             if (ok) {
                 const uint32_t slot = atomicAdd(&sb_cnt[sb], 1u);
@@ -565,7 +570,7 @@ __device__ bool fold_staged(unsigned char* smem, const DevPlan& dp, const DevCur
 #pragma unroll
         for (int u = 0; u < kPerThread; ++u) {
             const uint32_t q = threadIdx.x + u * kFoldThreads;
-            const uint32_t f = fold_fine((long long)(kv[u] >> ib), sh, mul, fshift) & kFineMask;
+            const uint32_t f = fold_fine((long long)(kv[u] >> ib), sh, mulf) & kFineMask;
             if (u & 1) kf[u >> 1] |= f << 16;
             else kf[u >> 1] = f;
             if (q < len) atomicAdd(&fcnt[f], 1u);
@@ -2171,10 +2176,10 @@ gtls_status create_device(gtls_plan* pl)
     dp.idx_bits = h.idx_bits;
     dp.bucket_log2 = h.bucket_log2;
     {
-        // super-buckets of the staged fold: about 4096 points each on average
-        int sb = 0;
-        while (sb < kFoldMaxSbLog2 && (h.n >> sb) > kFoldSegKeys / 2) ++sb;
-        dp.fold_sb_log2 = sb;
+        // super-buckets of the staged fold: about kFoldFillKeys points each
+        // on average (regions of kFoldSegKeys slots)
+        const int64_t nsb = (h.n + kFoldFillKeys - 1) / kFoldFillKeys;
+        dp.fold_nsb = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nsb, 1 << kFoldMaxSbLog2));
     }
     dp.max_kept = h.max_kept;
     dp.median_half = h.median_window / 2;
@@ -2236,7 +2241,7 @@ gtls_status create_device(gtls_plan* pl)
 
     DevChunk& dk = pl->dk;
     dk.fold_stride = (n + 31) & ~int64_t(31);
-    dk.key_stride = std::max<int64_t>(dk.fold_stride, (int64_t)kFoldSegKeys << dp.fold_sb_log2);
+    dk.key_stride = std::max<int64_t>(dk.fold_stride, (int64_t)kFoldSegKeys * dp.fold_nsb);
     dk.pad_stride = (n + h.dmax + kPadMargin + 31) & ~int64_t(31);
     const int64_t per_period = dk.key_stride * 8 + dk.fold_stride * 4 + dk.pad_stride * (4 + 4 + 4 + 8);
     // 8 GiB of chunk scratch (measured on the Kepler-like search: 1024,
