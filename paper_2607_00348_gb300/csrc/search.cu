@@ -1166,6 +1166,7 @@ k_window_tiles(DevSet ds, const __grid_constant__ SlotMap smv, const SlotMap* sm
             switch (t.variant) {
             case kWin16: warp_task_winpair<16, 3>(c, lane, best); break;
             case kCol16: warp_task_colpair<16, 3>(c, lane, best); break;
+            case kCol16R: warp_task_colpair_rot<16, 3>(c, lane, best); break;
             case kCol15: warp_task_colpair<15, 4>(c, lane, best); break;
             case kCol12: warp_task_colpair<12, 3>(c, lane, best); break;
             case kWeighted15: warp_task_weighted<15, 4>(c, lane, best); break;
@@ -2076,6 +2077,11 @@ gtls_status upload(gtls_plan* pl, T** ptr, const std::vector<T>& v)
 // much as 80 evaluations (about 20 for the (C1, S) pairs).
 void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out)
 {
+    // column pairs with rotated rounds: their two-way bank conflicts priced
+    // against the conflict-free 16-window variant (GTLS_COL16R_BASE
+    // overrides it; 0 disables the variant)
+    double kCol16RBase = 280.0;
+    if (const char* e = std::getenv("GTLS_COL16R_BASE")) kCol16RBase = std::atof(e);
     int v = 0;
     while (v < 5 && ((st >> v) & 1) == 0) ++v;
     double best = 1e300;
@@ -2094,6 +2100,7 @@ void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out
         switch (var) {
         case tiles::kCol15: base = 220.0; epi = 80.0; break;
         case tiles::kCol16: base = 255.0; epi = 80.0; break;
+        case tiles::kCol16R: base = kCol16RBase; epi = 80.0; break;
         case tiles::kCol12: base = 320.0; epi = 80.0; break;
         case tiles::kWin16: base = 320.0; epi = 80.0; break;
         default: base = 280.0 + 13.0 * st; epi = 20.0; break;   // (C1, S) pairs: two lanes per evaluation
@@ -2115,6 +2122,8 @@ void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out
     }
     if (v + 2 <= 5) consider(tiles::kCol12, 1 << (v + 2));
     if (v + 4 <= 5) consider(tiles::kCol16, 1 << (v + 4));
+    if (v >= 1 && kCol16RBase > 0.0)
+        for (int nc = 2; nc <= 16; nc <<= 1) consider(tiles::kCol16R, nc);
 }
 
 int fold_smem_bytes(int bucket_log2)

@@ -67,6 +67,7 @@ enum Variant : int {
     kCol12 = 8,
     kCol8 = 9,
     kWeighted15 = 10,   // per-point weights: (w r, w) tile pairs x (s_k, s_k^2) template pairs
+    kCol16R = 11,       // column pairs, 16 windows, rounds rotated by block (W st = 0 mod 32)
     kWindowOnly = 12,   // duration too long for a tile: the one-thread-per-window kernel takes it
     kTensor = 13,       // uniform weights: the tensor-core kernel (window_tc.cuh) takes it
 };
@@ -80,6 +81,7 @@ __host__ __device__ inline int variant_w(int v)
     case kWin12: return 12;
     case kWin8: return 8;
     case kCol16: return 16;
+    case kCol16R: return 16;
     case kCol15: return 15;
     case kCol14: return 14;
     case kCol12: return 12;
@@ -88,7 +90,7 @@ __host__ __device__ inline int variant_w(int v)
     }
 }
 
-__host__ __device__ inline bool variant_colpair(int v) { return v >= kCol16 && v <= kCol8; }
+__host__ __device__ inline bool variant_colpair(int v) { return (v >= kCol16 && v <= kCol8) || v == kCol16R; }
 
 struct DurTask {
     int j, d, st, nc, variant, w, per_task, tasks, first, m_a, m_b, hi_start, m_total, jrows;
@@ -291,6 +293,60 @@ __device__ void warp_task_colpair(const WinCtx& c, int lane, unsigned long long&
                 ring[r] = nxt[r];
                 nxt[r] = __ldg(c.tg2 + rho + 2 * nc + r * st);   // next round (zero padded)
             }
+            const float2* tp = c.tg2 + rho + R * st;
+            float2 p[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                p[w].x = a[w * st];
+                p[w].y = a[w * st + nc];
+            }
+            const float* an = a + W * st;
+            int jj = 0;
+            for (; jj + W <= jrows; jj += W) colpair_rows<W, R, true>(acc, p, ring, tp, an, st, nc, W);
+            if (jj < jrows) colpair_rows<W, R, false>(acc, p, ring, tp, an, st, nc, jrows - jj);
+        }
+    }
+    float tot[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) tot[w] = acc[w].x + acc[w].y;
+    reduce_finish<W>(c, tot, mb, active, lane, best);
+}
+
+// Column pairs with rotated rounds (any T0 step with W st = 0 mod 32, where
+// every block of W windows would read the same banks): block b walks its
+// column rounds starting at round b (mod the round count), so that at a
+// given time the blocks read columns 2 nc apart (at most two blocks per
+// bank).  Every lane still covers its columns once, in another order.
+template <int W, int R>
+__device__ void warp_task_colpair_rot(const WinCtx& c, int lane, unsigned long long& best)
+{
+    static_assert(W % (R + 1) == 0, "template ring length must divide the unroll period");
+    const int b = lane >> c.lg_nc;
+    const int cl = lane & (c.nc - 1);
+    bool active;
+    const int mb = block_start(c, b, W, active);
+    const int st = c.st, nc = c.nc, jrows = c.jrows;
+    float2 acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = make_float2(0.0f, 0.0f);
+    if (active) {
+        const float* abase = c.tile + (mb * st - c.x0);
+        const int rounds = (st + 2 * nc - 1) / (2 * nc);
+        int rr = b % rounds;
+        float2 nxt[R];   // first R template rows of the coming column round
+#pragma unroll
+        for (int r = 0; r < R; ++r) nxt[r] = __ldg(c.tg2 + cl + 2 * nc * rr + r * st);
+        for (int k = 0; k < rounds; ++k) {
+            const int rho = cl + 2 * nc * rr;
+            rr = rr + 1 == rounds ? 0 : rr + 1;
+            float2 ring[R + 1];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ring[r] = nxt[r];
+                nxt[r] = __ldg(c.tg2 + cl + 2 * nc * rr + r * st);   // next round (zero padded)
+            }
+            if (rho >= st) continue;
+            const float* a = abase + rho;
             const float2* tp = c.tg2 + rho + R * st;
             float2 p[W];
 #pragma unroll
