@@ -24,6 +24,10 @@
 //     colpair<W>  one FFMA2 per window covers the two columns rho, rho + nc
 //                 (template pairs come from a per-duration pair table whose
 //                 second value is zero where rho + nc >= st);  W = 16, 15, 12
+//     colpair_rot<16> the same for even T0 steps with any nc, each block
+//                 walking its column rounds from round b on, so that the
+//                 blocks (whose rows are 16 st = 0 mod 32 floats apart) read
+//                 different banks but in pairs;
 //     winpair<16> one FFMA2 covers windows w and w + 8 of one column
 //                 (T0 steps that are multiples of 32);
 //     scalar<15>  T0 steps 1, 2, 4, 8, 16 (one column per lane): each FFMA2
