@@ -250,12 +250,13 @@ gtls_status gtls_batch_search(gtls_batch* batch, const double* t, const double* 
                               const int64_t* offsets, void* stream, gtls_result* out);
 
 /*
- * Choose the wave size (the largest, a half, a quarter) and the staged tile
- * size (the plans' own, 49152, 40960, 32768, 24576 floats) by timing the coarse pass of
- * a probe (four runs of 256 periods spread over each of the first four
- * curves that take the tiled kernel) on these inputs; keeps the fastest.
- * Results do not depend on the choice.  Same arguments as
- * gtls_batch_search.
+ * Choose the wave size (the largest, a half, a quarter) by timing the
+ * coarse pass of a probe (four runs of 256 periods spread over each of the
+ * first four curves that take the tiled kernel) on these inputs; keeps the
+ * fastest.  The staged tile stays the plans' own (the tile decomposition
+ * fixes the order in which some window variants sum a window, so it must
+ * match the single-curve search).  Results do not depend on the choice.
+ * Same arguments as gtls_batch_search.
  */
 gtls_status gtls_batch_autotune(gtls_batch* batch, const double* t, const double* y, const double* dy,
                                 const int64_t* offsets, void* stream);

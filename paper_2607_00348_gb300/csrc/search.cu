@@ -3563,9 +3563,12 @@ gtls_status batch_autotune(gtls_batch* b, const double* t, const double* y, cons
     for (int sc : {b->max_slots, b->max_slots / 2, b->max_slots / 4})
         if (sc >= 128 && std::find(slot_c.begin(), slot_c.end(), sc) == slot_c.end()) slot_c.push_back(sc);
     if (slot_c.empty()) slot_c.push_back(b->max_slots);
-    for (int bc : {b->tile_buf_max, 49152, 40960, 32768, 24576})
-        if (bc <= b->tile_buf_cap && bc >= 16384 && std::find(buf_c.begin(), buf_c.end(), bc) == buf_c.end())
-            buf_c.push_back(bc);
+    // the staged tile stays the plans' own: the tile decomposition decides
+    // which warp block evaluates a window, and the rotated column-pair
+    // variant sums a window's column rounds in an order that depends on its
+    // block, so another tile size would change results in the last bits
+    // against the curves searched alone
+    buf_c.push_back(b->tile_buf_max);
     cudaEvent_t e0, e1;
     GTLS_CUDA(cudaEventCreate(&e0));
     GTLS_CUDA(cudaEventCreate(&e1));

@@ -229,3 +229,22 @@ def test_many_short_grids_fill_waves_up_to_the_segment_limit():
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_autotuned_batch_of_multi_tile_curves_equals_single_searches():
+    # curves long enough for two staged tiles each, so that the tile
+    # decomposition (which decides the warp block that evaluates a window,
+    # and with it the summation order of some window variants) matters
+    import paper_2607_00348_gb300 as pkg
+    curves = [(lc.t, lc.y, lc.dy, dict(lc.search))
+              for lc in synth.batch_kepler_like(2, seed=11, n_min=44000, n_max=46000)]
+    plans = _plans(curves)
+    singles = [gh.gpu_search(p, c[0], c[1], c[2]) for p, c in zip(plans, curves)]
+    t, y, dy, offs = _packed(curves)
+    batch = pkg.Batch(plans)
+    batch.autotune(t, y, dy, offs)
+    res = batch.search(t, y, dy, offs)
+    _same(batch, plans, res, singles)
+    batch.close()
+    for p in plans:
+        p.close()
