@@ -71,7 +71,7 @@ constexpr int kFoldThreads = 1024;
 constexpr int kFoldMinBlocks = 1;     // fold CTAs per SM the register budget is sized for
 constexpr int kFoldUnroll = 4;        // points whose loads a fold thread issues together
 constexpr int kFoldSegKeys = 8192;    // sort keys (and folded rfx) staged in shared memory per run of buckets
-constexpr int kRankBatch = 4;         // keys a fold thread ranks before issuing their gathers
+constexpr int kRankBatch = 2;         // keys a fold thread ranks before issuing their gathers (1, 2, 4, 8: 240.0, 240.3, 245.9, 272.8 ms)
 constexpr int kScanPer = 8;           // consecutive prefix-sum positions per fold thread
 constexpr int kWeightedTilePairs = 24576;   // (w r, w) pairs staged per tile with per-point weights
 constexpr int kSearchThreads = 256;
