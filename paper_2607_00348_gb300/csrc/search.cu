@@ -2069,8 +2069,8 @@ gtls_status upload(gtls_plan* pl, T** ptr, const std::vector<T>& v)
 // task x share of a window's time spent on its points).  The intrinsic
 // costs are warp cycles per 1000 issued FMA lanes, fitted to clock64
 // timings of every task of a Kepler-like search: 15-window column pairs
-// 220 (200 after a sweep of the bench's window stage), 16-window 255,
-// 12-window and window pairs 320, rotated 16-window pairs 280 (swept); the (C1, S) pairs
+// 220, 16-window 255, 12-window and window pairs 320, rotated 16-window
+// pairs 280 (swept on the bench's window stage); the (C1, S) pairs
 // spend two lanes per evaluation and their nc = st lanes per block a
 // recursive halving that grows with st (280 + 13 st per 1000 evaluations)
 // but finish a window without prefix-sum reads.  A window's epilogue
@@ -2099,7 +2099,7 @@ void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out
         const double fill = (double)nwin / (double)(tasks * per);
         double base, epi;
         switch (var) {
-        case tiles::kCol15: base = 200.0; epi = 80.0; break;
+        case tiles::kCol15: base = 220.0; epi = 80.0; break;
         case tiles::kCol16: base = 255.0; epi = 80.0; break;
         case tiles::kCol16R: base = kCol16RBase; epi = 80.0; break;
         case tiles::kCol12: base = 320.0; epi = 80.0; break;
@@ -2123,7 +2123,10 @@ void pick_config_host(int d, int st, int nwin, int32_t& variant, int32_t& nc_out
     }
     if (v + 2 <= 5) consider(tiles::kCol12, 1 << (v + 2));
     if (v + 4 <= 5) consider(tiles::kCol16, 1 << (v + 4));
-    if (v >= 1 && kCol16RBase > 0.0)
+    // (measured per T0-step class on the Kepler-like and 3000-day searches:
+    // 260-290 cycles per 1000 evaluations at steps 32-127, slower than the
+    // other variants below and above that range)
+    if (v >= 1 && kCol16RBase > 0.0 && st >= 32 && st < 128)
         for (int nc = 2; nc <= 16; nc <<= 1) consider(tiles::kCol16R, nc);
 }
 
