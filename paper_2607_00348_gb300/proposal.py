@@ -60,10 +60,10 @@ def _gen(args):
     return [(lc.t, lc.y, lc.dy, dict(lc.injected), float(lc.baseline_days)) for lc in lcs]
 
 
-def curve_chunks(seed, total, pool=None, chunk=CHUNK):
-    """Curves 0 .. total-1 of the uneven-length Kepler-like sequence `seed`,
-    in chunks of (t, y, dy, injected, baseline) tuples."""
-    jobs = [(seed, s, min(chunk, total - s)) for s in range(0, total, chunk)]
+def curve_chunks(seed, total, pool=None, chunk=CHUNK, start=0):
+    """Curves start .. start+total-1 of the uneven-length Kepler-like
+    sequence `seed`, in chunks of (t, y, dy, injected, baseline) tuples."""
+    jobs = [(seed, start + s, min(chunk, total - s)) for s in range(0, total, chunk)]
     if pool is None:
         for j in jobs:
             yield _gen(j)
@@ -280,14 +280,14 @@ def detected(res, inj, sde_min=9.0, rel=0.01):
 
 
 def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verify_sde=None,
-             verify_taus=()):
+             verify_taus=(), start=0):
     """Recall (SDE >= 9, period within 1 %) and light curves per hour of the
     plain batched search and of the proposal search at every tau (and, with
     verify_sde, at every tau of verify_taus with the verification fallback),
-    on curves 0 .. n_eval-1 of sequence `seed`; per curve, the injection, the
+    on curves start .. start+n_eval-1 of sequence `seed`; per curve, the injection, the
     plain result and the network's largest region score."""
     import torch
-    curves = [c for ch in curve_chunks(seed, n_eval, pool) for c in ch]
+    curves = [c for ch in curve_chunks(seed, n_eval, pool, start=start) for c in ch]
     full = [plan_for(c[0].size, c[4]) for c in curves]
     t, y, dy, offs = _pack(curves, dev)
     batch = _g.Batch(full)
@@ -300,7 +300,7 @@ def evaluate(net, n_eval, seed, dev, taus, frac=FRAC, pool=None, log=None, verif
     batch.close()
     inj = [c[3] for c in curves]
     n_inj = sum(1 for i in inj if i)
-    out = {"curves": n_eval, "injected": n_inj, "seed": seed, "frac": frac,
+    out = {"curves": n_eval, "injected": n_inj, "seed": seed, "start": start, "frac": frac,
            "plain": {"recall": sum(detected(r, i) for r, i in zip(plain, inj)) / max(n_inj, 1),
                      "false_alarms": sum(1 for r, i in zip(plain, inj) if not i and r.sde >= 9.0),
                      "seconds": plain_s, "lc_per_hour": n_eval * 3600.0 / plain_s},
@@ -401,6 +401,7 @@ def main(argv=None):
     ev.add_argument("--weights", default=WEIGHTS)
     ev.add_argument("--eval", type=int, default=64)
     ev.add_argument("--seed", type=int, default=5)
+    ev.add_argument("--start", type=int, default=0, help="first held-out curve of the sequence")
     ev.add_argument("--taus", default="0.0,0.3,0.5")
     ev.add_argument("--frac", type=float, default=FRAC)
     ev.add_argument("--verify-sde", type=float, default=None)
@@ -436,7 +437,7 @@ def main(argv=None):
         net = _g.Cnn(max(a.eval, 1), params)
         taus = [float(v) for v in a.taus.split(",")]
         vtaus = [float(v) for v in a.verify_taus.split(",") if v.strip()]
-        out = evaluate(net, a.eval, a.seed, dev, taus, frac=a.frac, pool=pool, log=log,
+        out = evaluate(net, a.eval, a.seed, dev, taus, frac=a.frac, pool=pool, log=log, start=a.start,
                        verify_sde=a.verify_sde, verify_taus=vtaus)
         out["weights"] = {k: v for k, v in meta.items() if k != "loss"}
         print(json.dumps(out))
