@@ -28,3 +28,43 @@ def test_library_parameter_layout_matches_the_reference():
     from paper_2607_00348_gb300 import proposal as pr
     n = sum(int(np.prod(s)) for _, s in cnn.param_shapes())
     assert pkg.gtls.load().gtls_cnn_param_count() == n == pr.init_params(0).size
+
+
+def test_triage_threshold_keeps_every_calibration_detection():
+    # brute force over a synthetic evaluation record: the threshold of each
+    # half is the smallest score of its plain detections, the other half is
+    # searched where its score reaches it, and the rates follow
+    from paper_2607_00348_gb300 import proposal as pr
+    rng = np.random.default_rng(3)
+    n = 40
+    per = []
+    for i in range(n):
+        inj = rng.uniform() < 0.5
+        det = bool(inj and rng.uniform() < 0.7)
+        per.append({"score_max": float(rng.uniform(0.3, 1.0) if det else rng.uniform(0.0, 0.8)),
+                    "plain_detected": det, "inj_period": 3.0 if inj else None})
+    rows = pr.triage(per, 1000.0)
+    assert len(rows) == 2
+    halves = (range(0, n // 2), range(n // 2, n))
+    for row, (cal, test) in zip(rows, ((halves[0], halves[1]), (halves[1], halves[0]))):
+        thr = min(per[i]["score_max"] for i in cal if per[i]["plain_detected"])
+        assert row["threshold"] == thr
+        keep = [i for i in test if per[i]["score_max"] >= thr]
+        assert row["searched"] == len(keep) and row["curves"] == len(test)
+        assert row["detections_kept"] == sum(per[i]["plain_detected"] for i in keep)
+        assert row["detections_plain"] == sum(per[i]["plain_detected"] for i in test)
+        n_inj = sum(per[i]["inj_period"] is not None for i in test)
+        assert row["recall"] == row["detections_kept"] / n_inj
+        assert abs(row["lc_per_hour"] - 1000.0 * len(test) / len(keep)) < 1e-9
+
+
+def test_triage_threshold_of_the_stored_evaluation():
+    # the bench's learned leg reads the smaller cross-validated threshold
+    import json
+    import os
+    from paper_2607_00348_gb300 import proposal as pr
+    path = os.path.join(os.path.dirname(pr.WEIGHTS), "proposal_eval.json")
+    with open(path) as f:
+        rows = json.load(f)["triage"]
+    assert pr.triage_threshold() == min(r["threshold"] for r in rows)
+    assert all(r["detections_kept"] <= r["detections_plain"] for r in rows)
